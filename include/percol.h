@@ -1,0 +1,129 @@
+/*
+ * percol.h -- C ABI of libpercol, a GB300 (sm_103a) implementation of the
+ * Markov-chain percolation inspection of F. Xu, Z. Xu and B. I. Yakobson,
+ * "Site-Percolation Threshold of Carbon Nanotube Fibers -- Fast Inspection of
+ * Percolation with Markov Stochastic Theory" (arXiv:1401.2130).
+ *
+ * The method (Sec. II.B, Eqs. (1)-(4), Appendix Eq. (A.3)): for one random
+ * configuration of the modified-FCC fibre lattice (Sec. II.A), a random walk
+ * over metallic sites with P_ij = 1/deg(i) (Eq. (2)) is started from the
+ * metallic sites of one fibre end; repeated sparse matrix-vector products
+ * propagate its probability mass until the first step m at which mass reaches
+ * the detector site joined to every metallic site of the other end (the
+ * configuration percolates; m - 1 is the length of the shortest spanning
+ * path), or until the set of reached sites stops growing (it does not).
+ * Pi(p) is the fraction of percolating configurations (Sec. III).
+ *
+ * Geometry (Sec. II.A): columns (q, r) of a hexagon of radius W in axial
+ * coordinates, max(|q|, |r|, |q + r|) <= W, A = 3W(W+1)+1 columns, L tubes
+ * per column, N = A*L sites.  Site id i = t*A + a, a = column rank in
+ * row-major order (r = -W..W, q ascending), t = 0..L-1 along the fibre.
+ * Each site has 12 side contacts (the FCC nearest neighbours) and 2 end
+ * contacts (same column, t +- 1).  Mass starts uniformly on the metallic
+ * sites of t = 0; the detector is joined to the metallic sites of t = L-1.
+ *
+ * Occupancy (Sec. II.A, Bernoulli(p) per site) comes from Philox4x32-10
+ * (Salmon et al., SC'11) with key = (seed & 0xffffffff, seed >> 32),
+ * counter = (i >> 2, config_index, W | (L << 8), 0); site i is metallic iff
+ * output word (i & 3) < floor(p * 2^32).  Bit-packed occupancy stores site i
+ * in bit (i & 31) of 32-bit word (i >> 5) of its configuration.
+ *
+ * Conventions for every call:
+ *  - Returns PC_OK (0) or a negative pc_status; pc_last_error() then holds a
+ *    thread-local message.  No call aborts the process.
+ *  - The caller owns every buffer it passes.  The library owns only its own
+ *    device scratch (stream-ordered, released before the call returns for
+ *    host outputs, or in stream order for device outputs) and a per-device
+ *    cache of lattice tables released by pc_shutdown().
+ *  - cuda_stream is a cudaStream_t or NULL (legacy default stream).  Work is
+ *    enqueued on it; with host outputs the call synchronises that stream
+ *    before returning, with PC_OUT_DEVICE it returns without synchronising.
+ *  - Results do not depend on batching, stream or placement: the generator
+ *    is counter based and all reductions that decide results are integer.
+ *  - Argument rules: 0 <= W <= 255, 1 <= L < 2^24, 0 <= p <= 1 (not NaN),
+ *    n_configs >= 0, 0 <= config_begin, config_begin + n_configs <= 2^32.
+ */
+#ifndef PERCOL_H
+#define PERCOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pc_status;
+
+#define PC_OK 0
+#define PC_ERR_ARG (-1)        /* invalid argument */
+#define PC_ERR_OOM (-2)        /* device memory or footprint budget exceeded */
+#define PC_ERR_CUDA (-3)       /* a CUDA runtime call failed */
+#define PC_ERR_TIMEOUT (-4)    /* a bounded wait expired */
+#define PC_ERR_BUSY (-5)       /* result not ready yet (server poll) */
+#define PC_ERR_CANCELLED (-6)  /* query cancelled or server shut down */
+#define PC_ERR_INTERNAL (-7)   /* an internal consistency check failed */
+
+/* flags */
+#define PC_OUT_DEVICE 0x1      /* per-configuration outputs and n_percolating
+                                  are device pointers; Pi must be NULL */
+#define PC_MODE_RESIDENT 0x10  /* force the shared-memory resident solver */
+#define PC_MODE_STREAM 0x20    /* force the streamed (global memory) solver */
+
+/*
+ * Lattice size (Sec. II.A): n_columns = A = 3W(W+1)+1, n_sites = A*L.
+ * Either pointer may be NULL.  Errors: PC_ERR_ARG.
+ */
+pc_status pc_lattice_info(int32_t W, int32_t L, int64_t* n_columns, int64_t* n_sites);
+
+/*
+ * Draw the occupancy of configurations config_begin .. +n_configs-1
+ * (Sec. II.A) into occ_bits, a DEVICE buffer of n_configs * ceil(N/32)
+ * uint32 words, configuration-major, bit-packed in site order.  Asynchronous
+ * on cuda_stream.  Errors: PC_ERR_ARG, PC_ERR_CUDA.
+ */
+pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed,
+                       int64_t config_begin, int64_t n_configs,
+                       uint32_t* occ_bits, void* cuda_stream);
+
+/*
+ * Inspect configurations config_begin .. +n_configs-1 at probability p
+ * (Sec. II.B; Pi(p) of Sec. III).  Per-configuration outputs, each
+ * [n_configs] and each optional except verdicts:
+ *   verdicts  : 1 if the configuration percolates, else 0
+ *   first_hit : first step m with non-zero detector probability (Eq. (3));
+ *               first_hit - 1 = shortest spanning path length; -1 if none
+ *   mass      : FP32 detector probability at first_hit (the first-passage
+ *               probability averaged over the start sites); 0 if none
+ *   m_stop    : steps taken: first_hit if percolating, else the first step
+ *               whose reached set did not grow; 0 if no start site is metallic
+ * n_percolating (int64) and Pi (= n_percolating / n_configs) are optional.
+ * Outputs are host pointers unless flags has PC_OUT_DEVICE.
+ * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
+ */
+pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed,
+                     int64_t config_begin, int64_t n_configs,
+                     uint8_t* verdicts, int32_t* first_hit, float* mass,
+                     int32_t* m_stop, int64_t* n_percolating, double* Pi,
+                     int32_t flags, void* cuda_stream);
+
+/*
+ * As pc_inspect, for caller-given occupancies: occ_bits is a DEVICE buffer of
+ * n_configs * ceil(N/32) uint32 words in the layout pc_occupancy writes.
+ */
+pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits,
+                               int64_t n_configs, uint8_t* verdicts,
+                               int32_t* first_hit, float* mass, int32_t* m_stop,
+                               int64_t* n_percolating, double* Pi,
+                               int32_t flags, void* cuda_stream);
+
+/* Release cached lattice tables and scratch of every device. */
+pc_status pc_shutdown(void);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* pc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERCOL_H */

@@ -1,0 +1,210 @@
+"""GB300-native percolation inspection (Xu, Xu & Yakobson, arXiv:1401.2130).
+
+Thin Python binding of ``libpercol.so`` (C ABI in ``include/percol.h``).  The
+functions keep the C names and only marshal arguments: every step of the
+inspection runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpercol.so")
+
+PC_OK = 0
+PC_ERR_ARG = -1
+PC_ERR_OOM = -2
+PC_ERR_CUDA = -3
+PC_ERR_TIMEOUT = -4
+PC_ERR_BUSY = -5
+PC_ERR_CANCELLED = -6
+PC_ERR_INTERNAL = -7
+PC_OUT_DEVICE = 0x1
+PC_MODE_RESIDENT = 0x10
+PC_MODE_STREAM = 0x20
+
+_STATUS = {PC_ERR_ARG: "PC_ERR_ARG", PC_ERR_OOM: "PC_ERR_OOM", PC_ERR_CUDA: "PC_ERR_CUDA",
+           PC_ERR_TIMEOUT: "PC_ERR_TIMEOUT", PC_ERR_BUSY: "PC_ERR_BUSY",
+           PC_ERR_CANCELLED: "PC_ERR_CANCELLED", PC_ERR_INTERNAL: "PC_ERR_INTERNAL"}
+
+# Every symbol include/percol.h declares, with its ctypes signature.
+_i32, _i64, _u64, _dbl, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                               ctypes.c_double, ctypes.c_void_p)
+SIGNATURES = {
+    "pc_lattice_info": [_i32, _i32, _vp, _vp],
+    "pc_occupancy": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp],
+    "pc_inspect": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
+    "pc_inspect_occupancy": [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
+    "pc_shutdown": [],
+    "pc_last_error": [],
+}
+
+
+class PercolError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libpercol.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, args in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "pc_last_error" else ctypes.c_int32
+    _lib = lib
+    return lib
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def _check(st: int):
+    if st != PC_OK:
+        msg = load().pc_last_error()
+        raise PercolError(st, msg.decode() if msg else "")
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def pc_lattice_info(W: int, L: int) -> tuple[int, int]:
+    """(A, N): columns of the hexagon of radius W and A*L sites (Sec. II.A)."""
+    a = ctypes.c_int64(); n = ctypes.c_int64()
+    _check(load().pc_lattice_info(W, L, ctypes.byref(a), ctypes.byref(n)))
+    return a.value, n.value
+
+
+def words_per_config(W: int, L: int) -> int:
+    return (pc_lattice_info(W, L)[1] + 31) // 32
+
+
+def pc_occupancy(W: int, L: int, p: float, seed: int, config_begin: int, n_configs: int,
+                 out=None, stream=None):
+    """Bit-packed occupancy [n_configs, ceil(N/32)] (int32 view of uint32 words)
+    on the current CUDA device (Sec. II.A)."""
+    import torch
+    wpc = words_per_config(W, L)
+    if out is None:
+        out = torch.empty((n_configs, wpc), dtype=torch.int32, device="cuda")
+    assert out.is_cuda and out.is_contiguous() and out.numel() >= n_configs * wpc
+    _check(load().pc_occupancy(W, L, float(p), int(seed) & (2**64 - 1), config_begin,
+                               n_configs, _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def _alloc_outputs(n: int, device: bool, want: tuple):
+    if device:
+        import torch
+        mk = lambda dt: torch.empty(n, dtype=dt, device="cuda")
+        out = {"verdict": mk(torch.uint8)}
+        if "first_hit" in want: out["first_hit"] = mk(torch.int32)
+        if "mass" in want: out["mass"] = mk(torch.float32)
+        if "m_stop" in want: out["m_stop"] = mk(torch.int32)
+        out["n_percolating"] = torch.zeros(1, dtype=torch.int64, device="cuda")
+        return out
+    out = {"verdict": np.zeros(n, np.uint8)}
+    if "first_hit" in want: out["first_hit"] = np.zeros(n, np.int32)
+    if "mass" in want: out["mass"] = np.zeros(n, np.float32)
+    if "m_stop" in want: out["m_stop"] = np.zeros(n, np.int32)
+    return out
+
+
+ALL_OUTPUTS = ("first_hit", "mass", "m_stop")
+
+
+def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs: int, *,
+               device: bool = False, want: tuple = ALL_OUTPUTS, mode: int = 0,
+               stream=None, out: dict | None = None) -> dict:
+    """Inspect configurations config_begin..+n_configs-1 (Sec. II.B, Eqs. (1)-(4)).
+
+    device=False: numpy outputs plus ``n_percolating`` and ``Pi`` (the call
+    synchronises).  device=True: torch CUDA tensors written asynchronously on
+    ``stream``; ``n_percolating`` is a one-element int64 tensor.
+    ``out`` may pass preallocated outputs of the same form.
+    """
+    o = out if out is not None else _alloc_outputs(n_configs, device, want)
+    flags = mode | (PC_OUT_DEVICE if device else 0)
+    npc = ctypes.c_int64(0); pi = ctypes.c_double(0.0)
+    _check(load().pc_inspect(
+        W, L, float(p), int(seed) & (2**64 - 1), config_begin, n_configs,
+        _ptr(o["verdict"]), _ptr(o.get("first_hit")), _ptr(o.get("mass")), _ptr(o.get("m_stop")),
+        _ptr(o["n_percolating"]) if device else ctypes.addressof(npc),
+        None if device else ctypes.addressof(pi), flags, _stream_handle(stream)))
+    if not device:
+        o["n_percolating"] = npc.value
+        o["Pi"] = pi.value
+    return o
+
+
+def pc_inspect_occupancy(W: int, L: int, occ_bits, *, device: bool = False,
+                         want: tuple = ALL_OUTPUTS, mode: int = 0, stream=None,
+                         out: dict | None = None) -> dict:
+    """As pc_inspect for caller occupancies: ``occ_bits`` is a CUDA int32/uint32
+    tensor [n_configs, ceil(N/32)] in pc_occupancy's layout."""
+    wpc = words_per_config(W, L)
+    assert occ_bits.is_cuda and occ_bits.is_contiguous() and occ_bits.element_size() == 4
+    n = occ_bits.numel() // wpc if occ_bits.numel() else 0
+    assert n * wpc == occ_bits.numel()
+    o = out if out is not None else _alloc_outputs(n, device, want)
+    flags = mode | (PC_OUT_DEVICE if device else 0)
+    npc = ctypes.c_int64(0); pi = ctypes.c_double(0.0)
+    _check(load().pc_inspect_occupancy(
+        W, L, _ptr(occ_bits), n,
+        _ptr(o["verdict"]), _ptr(o.get("first_hit")), _ptr(o.get("mass")), _ptr(o.get("m_stop")),
+        _ptr(o["n_percolating"]) if device else ctypes.addressof(npc),
+        None if device else ctypes.addressof(pi), flags, _stream_handle(stream)))
+    if not device:
+        o["n_percolating"] = npc.value
+        o["Pi"] = pi.value
+    return o
+
+
+def pc_shutdown():
+    _check(load().pc_shutdown())
+
+
+def site_updates(A: int, L: int, verdict, first_hit, m_stop) -> int:
+    """Site updates the forward recursion performed: every computed step m
+    sweeps the causal window of min(m + 1, L) layers of A sites.  A
+    percolating configuration computes steps 1..first_hit-1 (step first_hit
+    only reads the detector); a non-percolating one steps 1..m_stop."""
+    v = np.asarray(verdict).astype(np.int64)
+    fh = np.asarray(first_hit).astype(np.int64)
+    ms = np.asarray(m_stop).astype(np.int64)
+    M = np.maximum(np.where(v != 0, fh - 1, ms), 0)
+    k = np.minimum(M, L - 1)
+    s = k * (k + 3) // 2 + np.maximum(M - k, 0) * L
+    return int(s.sum()) * A

@@ -1,0 +1,112 @@
+// common.cuh -- device and host pieces shared by the libpercol kernels.
+//
+// Lattice of Sec. II.A (Fig. 1): columns (q, r) of a hexagon of radius W in
+// axial coordinates, sublattice sigma = (q - r) mod 3 (the A, B, C layers of
+// Fig. 1(b)), FCC layer height h = 3t + sigma.  Every site has 12 side
+// contacts -- the FCC nearest neighbours: 6 in its own (111) layer, 3 in the
+// layer above and 3 below -- and 2 end contacts (same column, t +- 1).
+// The 12 side contacts as column offsets, with the tube-index shift they
+// imply (a step of one layer up from sigma = 2 enters the next tube period):
+//   d = 0..5   same layer : (1,1) (2,-1) (1,-2) (-1,-1) (-2,1) (-1,2), dt = 0
+//   d = 6..8   layer up   : (1,0) (-1,1) (0,-1),            dt = [sigma == 2]
+//   d = 9..11  layer down : (-1,0) (1,-1) (0,1),            dt = -[sigma == 0]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/percol.h"
+
+namespace pc {
+
+constexpr int kLateral = 12;
+
+__host__ __device__ constexpr int dir_dq(int d) {
+  return d == 0 ? 1 : d == 1 ? 2 : d == 2 ? 1 : d == 3 ? -1 : d == 4 ? -2 : d == 5 ? -1
+       : d == 6 ? 1 : d == 7 ? -1 : d == 8 ? 0 : d == 9 ? -1 : d == 10 ? 1 : 0;
+}
+__host__ __device__ constexpr int dir_dr(int d) {
+  return d == 0 ? 1 : d == 1 ? -1 : d == 2 ? -2 : d == 3 ? -1 : d == 4 ? 1 : d == 5 ? 2
+       : d == 6 ? 0 : d == 7 ? 1 : d == 8 ? -1 : d == 9 ? 0 : d == 10 ? -1 : 1;
+}
+// tube-index shift of direction d for a column of sublattice sigma
+__host__ __device__ inline int dir_dt(int d, int sigma) {
+  return d < 6 ? 0 : d < 9 ? (sigma == 2 ? 1 : 0) : (sigma == 0 ? -1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (J. K. Salmon et al., "Parallel Random Numbers: As Easy as
+// 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplications whose high
+// halves are xored with the other two words and the round key; the key is
+// bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct u32x4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+  for (int i = 0; i < 10; ++i) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    u32x4 n;
+    n.x = (uint32_t)(p1 >> 32) ^ c.y ^ k0;
+    n.y = (uint32_t)p1;
+    n.z = (uint32_t)(p0 >> 32) ^ c.w ^ k1;
+    n.w = (uint32_t)p0;
+    c = n;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Occupancy stream of one configuration: word j (j = 0..3) of the block for
+// counter (block, config, W | L << 8, 0) decides site 4*block + j.
+struct OccStream {
+  uint32_t k0, k1, cfg, wl;
+  uint64_t T;  // threshold floor(p * 2^32); 2^32 = every site metallic
+  __device__ inline uint32_t block_bits(uint32_t block) const {
+    const u32x4 r = philox4x32_10(u32x4{block, cfg, wl, 0u}, k0, k1);
+    return (uint32_t)((uint64_t)r.x < T) | ((uint32_t)((uint64_t)r.y < T) << 1) |
+           ((uint32_t)((uint64_t)r.z < T) << 2) | ((uint32_t)((uint64_t)r.w < T) << 3);
+  }
+};
+
+inline uint64_t threshold_of(double p) {
+  // p * 2^32 is exact in double; floor gives the integer threshold
+  double v = p * 4294967296.0;
+  return (uint64_t)v;  // p >= 0, truncation == floor
+}
+
+// ---------------------------------------------------------------------------
+// Lattice description handed to kernels (all device pointers).
+// ---------------------------------------------------------------------------
+struct Lattice {
+  int W, L;
+  int A;         // columns
+  int64_t N;     // sites
+  int S;         // row stride of per-layer float arrays: A + 1 (column A is an always-zero sentinel)
+  int TW;        // 32-bit words per column for bit arrays along t: ceil(L / 32)
+  int TWP;       // TW + 2: one zero padding word before and after
+  const int32_t* nbr;   // [A][12] neighbour column or A (sentinel) if outside the hexagon
+  const int8_t* sigma;  // [A]
+};
+
+// error reporting (thread-local message), defined in api.cu
+void set_error(const std::string& msg);
+pc_status cuda_fail(cudaError_t e, const char* what);
+
+#define PC_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return pc::cuda_fail(e_, #call); \
+  } while (0)
+
+// Host-side lattice cache (lattice.cu).  Returns device tables for (W, L) on
+// the current device; built once and kept until pc_shutdown().
+pc_status get_lattice(int W, int L, Lattice* out);
+void release_lattices();
+
+int64_t n_columns(int W);
+
+}  // namespace pc
