@@ -116,6 +116,40 @@ pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits,
                                int64_t* n_percolating, double* Pi,
                                int32_t flags, void* cuda_stream);
 
+/*
+ * pc_inspect_static -- pc_inspect for callers that must not allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant of the
+ * resident (shared-memory) solver.
+ *
+ * Who needs it: processes whose framework has reserved the whole device for
+ * its own pool allocator, where a cudaMalloc fails or fragments that pool,
+ * and latency-critical loops that cannot afford cudaMalloc / cudaFree, which
+ * may synchronise the whole device.  This call performs no device allocation
+ * of any kind: its scratch (counters, lattice tables, device staging of the
+ * outputs) is one static device array of about 3.8 MB that every GPU loading
+ * the library holds until the process exits.
+ *
+ * Arguments and outputs as pc_inspect with host outputs (all output pointers
+ * are HOST pointers; verdicts required, the others optional); the call
+ * synchronises cuda_stream before returning.
+ * Limits: n_configs <= 262144; W <= 51 (at most 8192 columns); the lattice
+ * must fit the resident solver's shared memory.  Anything larger returns
+ * PC_ERR_ARG with a message, before any work is enqueued.
+ * Sharing: every call on a device uses the same static array, which keeps
+ * the previous call's contents; counters are cleared and tables rewritten on
+ * each call, but calls whose GPU work overlaps (e.g. on two streams) race on
+ * the array and must be serialised by the caller.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any
+ * stream capture starts.
+ * Errors: PC_ERR_ARG, PC_ERR_CUDA.
+ */
+pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t seed,
+                            int64_t config_begin, int64_t n_configs,
+                            uint8_t* verdicts, int32_t* first_hit, float* mass,
+                            int32_t* m_stop, int64_t* n_percolating, double* Pi,
+                            void* cuda_stream);
+
 /* Release cached lattice tables and scratch of every device. */
 pc_status pc_shutdown(void);
 

@@ -40,6 +40,7 @@ SIGNATURES = {
     "pc_occupancy": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp],
     "pc_inspect": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_occupancy": [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
+    "pc_inspect_static": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
 }
@@ -189,6 +190,23 @@ def pc_inspect_occupancy(W: int, L: int, occ_bits, *, device: bool = False,
     if not device:
         o["n_percolating"] = npc.value
         o["Pi"] = pi.value
+    return o
+
+
+def pc_inspect_static(W: int, L: int, p: float, seed: int, config_begin: int,
+                      n_configs: int, stream=None) -> dict:
+    """pc_inspect without device allocation (host outputs; see percol.h):
+    for callers that cannot call cudaMalloc, e.g. because their framework's
+    pool allocator owns the device memory, or because an allocation could
+    synchronise the device inside a latency-critical loop."""
+    o = _alloc_outputs(n_configs, False, ALL_OUTPUTS)
+    npc = ctypes.c_int64(0); pi = ctypes.c_double(0.0)
+    _check(load().pc_inspect_static(
+        W, L, float(p), int(seed) & (2**64 - 1), config_begin, n_configs,
+        _ptr(o["verdict"]), _ptr(o["first_hit"]), _ptr(o["mass"]), _ptr(o["m_stop"]),
+        ctypes.addressof(npc), ctypes.addressof(pi), _stream_handle(stream)))
+    o["n_percolating"] = npc.value
+    o["Pi"] = pi.value
     return o
 
 
