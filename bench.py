@@ -51,6 +51,17 @@ def site_updates(A, L_, verdict, first_hit, m_stop) -> int:
     return int((k * (k + 3) // 2 + np.maximum(M - k, 0) * L_).sum()) * A
 
 
+def shard_range(rank: int, n_per_rank: int) -> tuple[int, int]:
+    """Weak scaling: rank r owns configurations [r * n, (r + 1) * n) at every p.
+    Ranks share no data; the only cross-rank step is the timing maximum."""
+    return rank * n_per_rank, n_per_rank
+
+
+def aggregate(site_updates_per_rank: list[int], seconds_per_rank: list[float]) -> float:
+    """Whole-job throughput: all ranks' site updates over the slowest rank's time."""
+    return float(sum(site_updates_per_rank)) / max(seconds_per_rank)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -167,6 +178,118 @@ def run_reference(args):
     return 0
 
 
+# HBM traffic model of one site update of the streamed solver, from the
+# method's data: nu read 4 B + nu write 4 B + occupancy 1/8 B + reached-set
+# bit read and write 1/4 B (the per-unit figure of the measurement plan).
+HBM_BYTES_PER_SU = 8.375
+
+
+def batching_specs(n=10_000):
+    return [(Wb, Wb * r, 0.1533, 3, 0, n) for Wb in (4, 8, 16, 32) for r in (1, 2, 4, 8, 16, 32, 64)]
+
+
+def run_large(args, pc, torch):
+    """W = 64, L = 4096 (51.1 M sites), p in {0.14, 0.1533, 0.17}, 64
+    configurations each, seed 4: the streamed solver, HBM bound."""
+    Wl, Ll, seed, n = 64, 4096, 4, args.large_configs
+    ps = [0.14, 0.1533, 0.17]
+    A = 3 * Wl * (Wl + 1) + 1
+    stream = torch.cuda.current_stream()
+    outs = [pc._alloc_outputs(n, True, pc.ALL_OUTPUTS) for _ in ps]
+    for _ in range(args.warmup):  # warm-up on one configuration per p
+        for p in ps:
+            pc.pc_inspect(Wl, Ll, p, seed, 0, 1, device=True, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for i, p in enumerate(ps):
+                pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=True, out=outs[i], stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]) / 1e3)
+    su = 0
+    perc = []
+    for o in outs:
+        h = {k: v.cpu().numpy() for k, v in o.items()}
+        su += site_updates(A, Ll, h["verdict"], h["first_hit"], h["m_stop"])
+        perc.append(int(h["verdict"].sum()))
+    t = float(np.mean(times))
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = HBM_BYTES_PER_SU * su / t / 1e9
+    return {
+        "metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"large W=64 L=4096 p=0.14/0.1533/0.17 x {n} configs seed=4",
+                   "site_updates_per_step": su, "percolating_per_p": perc, "solver": "streamed",
+                   "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB)"},
+        "configs_per_s": n * len(ps) / t,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "model": f"{HBM_BYTES_PER_SU} B/site-update x site-updates / time of the whole "
+                              "solve (sweep + control kernels), peak = measured copy bandwidth"},
+        "clocks": clk.summary(),
+    }
+
+
+def run_batch(args, pc, torch):
+    """28 (W, L) queries of the finite-size-scaling set, 10^4 configurations
+    each at p = 0.1533, seed 3: one batched submission (cached CUDA graph)
+    against 28 plain one-lattice-per-launch calls."""
+    specs = batching_specs(args.batch_configs)
+    stream = torch.cuda.current_stream()
+    queries, outs = pc.batch_queries(specs, device=True)
+    plain_outs = [pc._alloc_outputs(sp[5], True, pc.ALL_OUTPUTS) for sp in specs]
+
+    def batched():
+        pc.pc_batch_run(specs, device=True, async_=True, stream=stream, outs=outs, queries=queries)
+
+    def plain():
+        for sp, o in zip(specs, plain_outs):
+            W_, L_, p_, seed_, b_, n_ = sp
+            pc.pc_inspect(W_, L_, p_, seed_, b_, n_, device=True, out=o, stream=stream)
+
+    def timed(fn, steps):
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream); fn(); e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.mean(ts))
+
+    for _ in range(args.warmup):
+        batched(); plain()
+    torch.cuda.synchronize()
+    with Clocks(0) as clk:
+        tb = timed(batched, args.steps)
+        tp = timed(plain, args.steps)
+    su, n_tot, same = 0, 0, True
+    for sp, o, po in zip(specs, outs, plain_outs):
+        W_, L_ = sp[0], sp[1]
+        h = {k: v.cpu().numpy() for k, v in o.items()}
+        hp = {k: v.cpu().numpy() for k, v in po.items()}
+        same &= all(np.array_equal(h[k], hp[k]) for k in ("verdict", "first_hit", "m_stop"))
+        su += site_updates(3 * W_ * (W_ + 1) + 1, L_, h["verdict"], h["first_hit"], h["m_stop"])
+        n_tot += sp[5]
+    return {
+        "metric": "configs/s (batched)", "value": n_tot / tb, "unit": "configs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tb * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batching W in {4,8,16,32} x L/W in {1..64}, p=0.1533, seed=3",
+                   "queries": len(specs), "configs_per_query": args.batch_configs,
+                   "l2": "no flush (per-launch working sets differ; see plain)"},
+        "plain_configs_per_s": n_tot / tp, "batched_over_plain": tp / tb,
+        "site_updates_per_s_batched": su / tb, "results_identical": bool(same),
+        "clocks": clk.summary(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,9 +299,23 @@ def main():
     ap.add_argument("--ref-per-p", type=int, default=200)
     ap.add_argument("--cpu-per-p", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs-per-p", type=int, default=N_CFG,
+                    help="smaller cases for profiling only; the benchmark workload is 10^4")
+    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch"])
+    ap.add_argument("--large-configs", type=int, default=64)
+    ap.add_argument("--batch-configs", type=int, default=10_000)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "psweep":
+        import torch
+        import paper_1401_2130_gb300 as pc
+        torch.cuda.set_device(0)
+        pc.build()
+        pc.load()
+        fn = run_large if args.workload == "large" else run_batch
+        print(json.dumps(fn(args, pc, torch)), flush=True)
+        return 0
 
     import torch
     import paper_1401_2130_gb300 as pc
@@ -191,16 +328,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pc.build()
     pc.load()
-    cfg0 = rank * N_CFG
+    n_cfg = args.configs_per_p
+    cfg0, _ = shard_range(rank, n_cfg)
     stream = torch.cuda.current_stream()
-    outs = [pc._alloc_outputs(N_CFG, True, pc.ALL_OUTPUTS) for _ in PS]
+    outs = [pc._alloc_outputs(n_cfg, True, pc.ALL_OUTPUTS) for _ in PS]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step(evs=None):
         for i, p in enumerate(PS):
             if evs is not None:
                 evs[i][0].record(stream)
-            pc.pc_inspect(W, L, p, SEED, cfg0, N_CFG, device=True, out=outs[i], stream=stream)
+            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=True, out=outs[i], stream=stream)
             if evs is not None:
                 evs[i][1].record(stream)
 
@@ -246,13 +384,13 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for p in PS:
-            pc.pc_inspect(W, L, p, SEED, cfg0, N_CFG, device=False)
+            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=False)
     e2e_t = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
         tt = torch.tensor([e2e_t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_t = float(tt.item())
-    d2h = len(PS) * (N_CFG * (1 + 4 + 4 + 4) + 8)
+    d2h = len(PS) * (n_cfg * (1 + 4 + 4 + 4) + 8)
 
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -266,13 +404,13 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "p-sweep W=8 L=64 p=0.100..0.200/0.005 seed=2",
-                   "W": W, "L": L, "n_p": len(PS), "configs_per_p": N_CFG,
-                   "configs_per_step": N_CFG * len(PS) * world,
+                   "W": W, "L": L, "n_p": len(PS), "configs_per_p": n_cfg,
+                   "configs_per_step": n_cfg * len(PS) * world,
                    "site_updates_per_step_per_gpu": su_step,
                    "percolating_per_p": n_perc, "solver": "resident",
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": f"configs sharded over {world} GPU(s)"},
-        "configs_per_s": N_CFG * len(PS) * world / t_step,
+        "configs_per_s": n_cfg * len(PS) * world / t_step,
         "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                      "frac": achieved / smem_peak, "traffic": None,
                      "model": f"{SMEM_BYTES_PER_SU} B of shared-memory traffic per site update; "

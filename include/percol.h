@@ -117,6 +117,53 @@ pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits,
                                int32_t flags, void* cuda_stream);
 
 /*
+ * One query of a batch: configurations config_begin .. +n_configs-1 of the
+ * lattice (W, L) at probability p with the stream of seed.  The output
+ * pointers are optional; they are device pointers if the batch flags have
+ * PC_OUT_DEVICE, else host pointers.  n_percolating receives the count.
+ */
+typedef struct pc_query {
+  int32_t W, L;
+  double p;
+  uint64_t seed;
+  int64_t config_begin, n_configs;
+  uint8_t* verdicts;        /* [n_configs] */
+  int32_t* first_hit;       /* [n_configs] */
+  float* mass;              /* [n_configs] */
+  int32_t* m_stop;          /* [n_configs] */
+  int64_t* n_percolating;   /* [1] */
+} pc_query;
+
+/* Host-side summary of one query of a batch. */
+typedef struct pc_result {
+  int64_t n_percolating;
+  double Pi;
+  int32_t solver;           /* 0 = shared-memory resident, 1 = streamed */
+  int32_t threads;          /* CTA size the resident solver ran with */
+} pc_result;
+
+/*
+ * Inspect many queries of mixed lattice sizes in one GPU submission (the
+ * batching of a finite-size-scaling sweep, Sec. III): every query whose
+ * configuration state fits one CTA's shared memory runs the resident solver
+ * (one persistent kernel per query, all concurrent), every other query shares
+ * one pool of streamed-solver slots that refill as configurations finish; the
+ * whole batch is one CUDA graph, built on the first call and replayed when
+ * the same batch (same queries and output pointers) is submitted again.  The
+ * resident CTA size of each (W, L) is picked by timing candidates on first
+ * use (autotuner; choices kept in memory and in the JSON file named by the
+ * environment variable PC_TUNE_FILE, if set).
+ * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
+ * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
+ * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.
+ * Results equal those of pc_inspect on each query.
+ * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
+ */
+#define PC_ASYNC 0x2
+pc_status pc_batch_run(const pc_query* queries, int64_t n_queries, pc_result* out,
+                       int32_t flags, void* cuda_stream);
+
+/*
  * pc_inspect_static -- pc_inspect for callers that must not allocate device
  * memory.  The paper has no counterpart: this is a deployment variant of the
  * resident (shared-memory) solver.

@@ -25,6 +25,7 @@ PC_ERR_BUSY = -5
 PC_ERR_CANCELLED = -6
 PC_ERR_INTERNAL = -7
 PC_OUT_DEVICE = 0x1
+PC_ASYNC = 0x2
 PC_MODE_RESIDENT = 0x10
 PC_MODE_STREAM = 0x20
 
@@ -41,6 +42,7 @@ SIGNATURES = {
     "pc_inspect": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_occupancy": [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_static": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pc_batch_run": [_vp, _i64, _vp, _i32, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
 }
@@ -208,6 +210,60 @@ def pc_inspect_static(W: int, L: int, p: float, seed: int, config_begin: int,
     o["n_percolating"] = npc.value
     o["Pi"] = pi.value
     return o
+
+
+class PcQuery(ctypes.Structure):
+    """Mirror of pc_query (include/percol.h)."""
+    _fields_ = [("W", ctypes.c_int32), ("L", ctypes.c_int32), ("p", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("config_begin", ctypes.c_int64),
+                ("n_configs", ctypes.c_int64), ("verdicts", ctypes.c_void_p),
+                ("first_hit", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("m_stop", ctypes.c_void_p), ("n_percolating", ctypes.c_void_p)]
+
+
+class PcResult(ctypes.Structure):
+    """Mirror of pc_result (include/percol.h)."""
+    _fields_ = [("n_percolating", ctypes.c_int64), ("Pi", ctypes.c_double),
+                ("solver", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+def batch_queries(specs, *, device: bool, outs: list | None = None):
+    """ctypes query array for specs [(W, L, p, seed, config_begin, n_configs)],
+    with outputs allocated (or taken from ``outs``) per query."""
+    outs = outs if outs is not None else [_alloc_outputs(sp[5], device, ALL_OUTPUTS) for sp in specs]
+    arr = (PcQuery * len(specs))()
+    for i, (W, L, p, seed, b, n) in enumerate(specs):
+        o = outs[i]
+        arr[i] = PcQuery(W, L, float(p), int(seed) & (2**64 - 1), b, n, _ptr(o["verdict"]),
+                         _ptr(o.get("first_hit")), _ptr(o.get("mass")), _ptr(o.get("m_stop")),
+                         _ptr(o["n_percolating"]) if device else None)
+    return arr, outs
+
+
+def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=None,
+                 outs: list | None = None, queries=None):
+    """Inspect a batch of queries [(W, L, p, seed, config_begin, n_configs)] in
+    one submission (one cached CUDA graph).  Returns (outs, results): per-query
+    outputs (numpy, or torch CUDA tensors with ``device``) and the host
+    summaries (None with ``async_``).  Passing the same ``outs`` (and
+    ``queries``) again replays the cached graph."""
+    if queries is None:
+        queries, outs = batch_queries(specs, device=device, outs=outs)
+    flags = (PC_OUT_DEVICE if device else 0) | (PC_ASYNC if async_ else 0)
+    res = None if async_ else (PcResult * len(specs))()
+    _check(load().pc_batch_run(ctypes.addressof(queries), len(specs),
+                               None if res is None else ctypes.addressof(res), flags,
+                               _stream_handle(stream)))
+    if res is None:
+        return outs, None
+    results = [{"n_percolating": r.n_percolating, "Pi": r.Pi,
+                "solver": "resident" if r.solver == 0 else "streamed", "threads": r.threads}
+               for r in res]
+    if not device:
+        for o, r in zip(outs, results):
+            o["n_percolating"] = r["n_percolating"]
+            o["Pi"] = r["Pi"]
+    return outs, results
 
 
 def pc_shutdown():

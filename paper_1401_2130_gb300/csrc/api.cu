@@ -44,6 +44,15 @@ pc_status check_range(int64_t config_begin, int64_t n_configs) {
   return PC_OK;
 }
 
+}  // namespace
+
+bool resident_fits(int A, int L) {
+  int dev = 0, max_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return A <= 32767 && resident_smem(A, L) <= (size_t)max_smem;
+}
+
 int resident_threads(int A, int L) {
   const int per = (L + 15) / 16;  // aim at ~16 tube layers per thread
   long long t = (long long)A * per;
@@ -52,6 +61,8 @@ int resident_threads(int A, int L) {
   if (t > 1024) t = 1024;
   return (int)t;
 }
+
+namespace {
 
 struct Scratch {
   unsigned long long* work = nullptr;
@@ -86,7 +97,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
   if (rc) return rc;
 
   // call scratch: counters (+ device copies of host outputs)
-  size_t bytes = 64;
+  size_t bytes = 64;  // work counter, percolating counter, streamed-solver error flag
   if (!dev_out) bytes += (size_t)n * (1 + 4 + 4 + 4) + 64;
   Scratch s;
   PC_CUDA(cudaMallocAsync((void**)&s.base, bytes, st));
@@ -142,6 +153,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       j.n_cfg = n; j.cfg0 = (uint32_t)cfg0;
       j.out.verdict = s.verdict; j.out.first_hit = s.first_hit; j.out.mass = s.mass;
       j.out.m_stop = s.m_stop; j.out.n_perc = s.n_perc;
+      j.error_out = (int*)(s.work + 2);
       rc = run_stream(j, st);
     }
     if (rc) break;
@@ -151,9 +163,12 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       if (e == cudaSuccess && mass) e = cudaMemcpyAsync(mass, s.mass, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess && m_stop) e = cudaMemcpyAsync(m_stop, s.m_stop, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
       unsigned long long cnt = 0;
+      int err = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, s.n_perc, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&err, s.work + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) { rc = cuda_fail(e, "copy outputs"); break; }
+      if (err) { set_error("streamed solver hit its tick bound"); rc = PC_ERR_INTERNAL; break; }
       if (n_percolating) *n_percolating = (int64_t)cnt;
       if (Pi) *Pi = (double)cnt / (double)n;
     }
@@ -228,6 +243,7 @@ pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits, i
 }
 
 pc_status pc_shutdown(void) {
+  release_batches();
   release_lattices();
   return PC_OK;
 }

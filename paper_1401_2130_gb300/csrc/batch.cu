@@ -1,0 +1,331 @@
+// batch.cu -- pc_batch_run (one GPU submission for many queries of mixed
+// lattice sizes) and the autotuner of the resident solver's CTA size.
+//
+// A batch becomes one CUDA graph:
+//   memset(counters) -> { resident kernel of query i, for every query whose
+//                         state fits shared memory (parallel graph branches,
+//                         so their persistent grids overlap and fill each
+//                         other's tails) }
+//                    -> { init -> WHILE(sweep, control) of the streamed solver
+//                         over all remaining queries, sharing one slot pool }
+// The instantiated graph and its device memory are cached per batch (same
+// queries, output pointers and flags) and replayed by later calls.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// Autotuner: per (W, L), the resident CTA size with the lowest measured time
+// on a sample of configurations; kept in memory and in PC_TUNE_FILE.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("PC_TUNE_FILE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  // format: {"W,L": T, ...}
+  int W, L, T;
+  int ch;
+  while ((ch = std::fgetc(f)) != EOF) {
+    if (ch != '"') continue;
+    if (std::fscanf(f, "%d,%d\": %d", &W, &L, &T) == 3 && T > 0) g_tune[{W, L}] = T;
+  }
+  std::fclose(f);
+}
+
+void tune_save() {
+  const char* path = std::getenv("PC_TUNE_FILE");
+  if (!path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fputs("{", f);
+  bool first = true;
+  for (auto& kv : g_tune) {
+    std::fprintf(f, "%s\"%d,%d\": %d", first ? "" : ", ", kv.first.first, kv.first.second, kv.second);
+    first = false;
+  }
+  std::fputs("}\n", f);
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load();
+  auto it = g_tune.find({lat.W, lat.L});
+  if (it != g_tune.end()) return it->second;
+  const int fallback = resident_threads(lat.A, lat.L);
+  const int64_t n = 2048;
+  char* mem = nullptr;
+  if (cudaMallocAsync((void**)&mem, 64 + n * 13, st) != cudaSuccess) return fallback;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = fallback;
+  float best_ms = 1e30f;
+  const int cand[] = {128, 256, 384, 512, 768, 1024};
+  for (int T : cand) {
+    ResidentArgs a;
+    a.lat = lat;
+    a.occ.k0 = (uint32_t)(seed & 0xffffffffu); a.occ.k1 = (uint32_t)(seed >> 32);
+    a.occ.cfg = 0; a.occ.wl = (uint32_t)lat.W | ((uint32_t)lat.L << 8); a.occ.T = threshold_of(p);
+    a.occ_bits = nullptr; a.words_per_cfg = (lat.N + 31) / 32;
+    a.n_cfg = n; a.cfg0 = 0x80000000u;  // a sample away from ordinary ranges
+    a.verdict = (uint8_t*)(mem + 64); a.first_hit = (int32_t*)(mem + 64 + n);
+    a.mass = (float*)(mem + 64 + 5 * n); a.m_stop = (int32_t*)(mem + 64 + 9 * n);
+    a.n_perc = (unsigned long long*)(mem + 8); a.work = (unsigned long long*)mem;
+    a.prep_chunk = 8;
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {
+      cudaMemsetAsync(mem, 0, 64, st);
+      cudaEventRecord(e0, st);
+      ok = launch_resident(a, T, st) == PC_OK;
+      cudaEventRecord(e1, st);
+      if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+      if (ok) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ok && ms < best_ms) { best_ms = ms; best = T; }
+    cudaGetLastError();  // a candidate that does not fit is simply skipped
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(mem, st);
+  cudaStreamSynchronize(st);
+  g_tune[{lat.W, lat.L}] = best;
+  tune_save();
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// Batch graphs
+// ---------------------------------------------------------------------------
+namespace {
+
+struct QueryPlan {
+  int solver = 0;    // 0 resident, 1 streamed
+  int threads = 0;
+  unsigned long long* n_perc = nullptr;  // device counter
+  uint8_t* v = nullptr; int32_t* fh = nullptr; float* mass = nullptr; int32_t* ms = nullptr;  // device outputs
+};
+
+struct BatchGraph {
+  std::string key;
+  int device = 0;
+  char* mem = nullptr;       // counters + host-output staging
+  size_t mem_bytes = 0;
+  StreamPlan* plan = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<QueryPlan> qp;
+};
+
+std::mutex g_batch_mu;
+std::list<BatchGraph*> g_batches;  // most recent first
+constexpr size_t kMaxCached = 8;
+
+void destroy_batch(BatchGraph* b) {
+  if (!b) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->plan) stream_plan_release(b->plan, 0);
+  if (b->mem) cudaFree(b->mem);
+  cudaDeviceSynchronize();
+  cudaSetDevice(cur);
+  delete b;
+}
+
+std::string batch_key(const pc_query* q, int64_t n, int32_t flags, int dev) {
+  std::string k((const char*)q, sizeof(pc_query) * (size_t)n);
+  k.append((const char*)&flags, sizeof(flags));
+  k.append((const char*)&dev, sizeof(dev));
+  return k;
+}
+
+pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t st, BatchGraph** out) {
+  const bool dev_out = (flags & PC_OUT_DEVICE) != 0;
+  BatchGraph* b = new BatchGraph();
+  cudaGetDevice(&b->device);
+  b->qp.resize(nq);
+  // device memory: per query 2 counters (+ staging of host outputs)
+  size_t bytes = 256 + (size_t)nq * 16;
+  if (!dev_out)
+    for (int64_t i = 0; i < nq; ++i) bytes += ((size_t)q[i].n_configs * 13 + 256) & ~(size_t)255;
+  b->mem_bytes = bytes;
+  cudaError_t e = cudaMalloc((void**)&b->mem, bytes);
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "batch memory"); }
+  pc_status rc = PC_OK;
+  std::vector<StreamQuery> sq;
+  do {
+    unsigned long long* ctr = (unsigned long long*)b->mem;  // [nq][2]: n_perc, work
+    char* stage = b->mem + 256 + (size_t)nq * 16;
+    if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess) { rc = cuda_fail(e, "graph create"); break; }
+    cudaMemsetParams mp = {};
+    mp.dst = b->mem; mp.value = 0; mp.elementSize = 1; mp.width = 256 + (size_t)nq * 16; mp.height = 1;
+    mp.pitch = 0;
+    cudaGraphNode_t n_zero;
+    if ((e = cudaGraphAddMemsetNode(&n_zero, b->graph, nullptr, 0, &mp)) != cudaSuccess) { rc = cuda_fail(e, "memset node"); break; }
+    for (int64_t i = 0; i < nq && rc == PC_OK; ++i) {
+      QueryPlan& P = b->qp[i];
+      P.n_perc = ctr + 2 * i;
+      if (dev_out) {
+        P.v = q[i].verdicts; P.fh = q[i].first_hit; P.mass = q[i].mass; P.ms = q[i].m_stop;
+      } else {
+        const size_t n = (size_t)q[i].n_configs;
+        P.fh = (int32_t*)stage; P.mass = (float*)(stage + 4 * n); P.ms = (int32_t*)(stage + 8 * n);
+        P.v = (uint8_t*)(stage + 12 * n);
+        stage += (n * 13 + 256) & ~(size_t)255;
+      }
+      if (q[i].n_configs == 0) continue;
+      Lattice lat;
+      if ((rc = get_lattice(q[i].W, q[i].L, &lat))) break;
+      OccStream os;
+      os.k0 = (uint32_t)(q[i].seed & 0xffffffffu); os.k1 = (uint32_t)(q[i].seed >> 32);
+      os.cfg = 0; os.wl = (uint32_t)q[i].W | ((uint32_t)q[i].L << 8); os.T = threshold_of(q[i].p);
+      if (resident_fits(lat.A, lat.L)) {
+        P.solver = 0;
+        P.threads = tuned_threads(lat, q[i].p, q[i].seed, st);
+        ResidentArgs a;
+        a.lat = lat; a.occ = os; a.occ_bits = nullptr; a.words_per_cfg = (lat.N + 31) / 32;
+        a.n_cfg = q[i].n_configs; a.cfg0 = (uint32_t)q[i].config_begin;
+        a.verdict = P.v; a.first_hit = P.fh; a.mass = P.mass; a.m_stop = P.ms;
+        a.n_perc = P.n_perc; a.work = ctr + 2 * i + 1; a.prep_chunk = 8;
+        if (!a.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
+        cudaGraphNode_t node;
+        rc = resident_add_node(a, P.threads, b->graph, &n_zero, 1, &node);
+      } else {
+        P.solver = 1;
+        StreamQuery s;
+        s.lat = lat; s.occ = os; s.occ_bits = nullptr; s.words_per_cfg = (lat.N + 31) / 32;
+        s.n_cfg = q[i].n_configs; s.cfg0 = (uint32_t)q[i].config_begin;
+        s.out.verdict = P.v; s.out.first_hit = P.fh; s.out.mass = P.mass; s.out.m_stop = P.ms;
+        s.out.n_perc = P.n_perc;
+        if (!s.out.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
+        sq.push_back(s);
+      }
+    }
+    if (rc) break;
+    if (!sq.empty()) {
+      // largest lattices first: long configurations start early
+      std::stable_sort(sq.begin(), sq.end(), [](const StreamQuery& x, const StreamQuery& y) {
+        return x.lat.N > y.lat.N;
+      });
+      if ((rc = stream_plan_create(sq.data(), (int)sq.size(), st, &b->plan))) break;
+      cudaGraphNode_t last;
+      if ((rc = stream_plan_add(b->plan, b->graph, &n_zero, 1, &last))) break;
+    }
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) { rc = cuda_fail(e, "graph instantiate"); break; }
+    // the plan's initialisation (on st) must be complete before any replay,
+    // which may come on another stream
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { rc = cuda_fail(e, "batch build sync"); break; }
+  } while (0);
+  if (rc) { destroy_batch(b); return rc; }
+  *out = b;
+  return PC_OK;
+}
+
+}  // namespace
+
+void release_batches() {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (BatchGraph* b : g_batches) destroy_batch(b);
+  g_batches.clear();
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out, int32_t flags,
+                                  void* cuda_stream) {
+  if (nq < 0 || (nq > 0 && !q)) { set_error("pc_batch_run: bad query array"); return PC_ERR_ARG; }
+  const bool dev_out = (flags & PC_OUT_DEVICE) != 0, async = (flags & PC_ASYNC) != 0;
+  if (async && (!dev_out || out)) { set_error("PC_ASYNC needs PC_OUT_DEVICE and out == NULL"); return PC_ERR_ARG; }
+  for (int64_t i = 0; i < nq; ++i) {
+    const pc_query& x = q[i];
+    if (x.W < 0 || x.W > 255 || x.L < 1 || x.L >= (1 << 24)) { set_error("pc_batch_run: bad W or L"); return PC_ERR_ARG; }
+    if ((n_columns(x.W) + 1) * ((int64_t)x.L + 2) >= ((int64_t)1 << 31)) { set_error("pc_batch_run: lattice too large"); return PC_ERR_ARG; }
+    if (!(x.p >= 0.0 && x.p <= 1.0)) { set_error("pc_batch_run: p must be in [0, 1]"); return PC_ERR_ARG; }
+    if (x.n_configs < 0 || x.config_begin < 0 || x.config_begin + x.n_configs > ((int64_t)1 << 32)) {
+      set_error("pc_batch_run: bad configuration range"); return PC_ERR_ARG;
+    }
+    if (x.n_configs > 0 && !x.verdicts) { set_error("pc_batch_run: verdicts must not be NULL"); return PC_ERR_ARG; }
+  }
+  if (nq == 0) return PC_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  PC_CUDA(cudaGetDevice(&dev));
+  const std::string key = batch_key(q, nq, flags, dev);
+  BatchGraph* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end(); ++it)
+      if ((*it)->key == key) { b = *it; g_batches.erase(it); g_batches.push_front(b); break; }
+  }
+  if (!b) {
+    pc_status rc = build_batch(q, nq, flags, st, &b);
+    if (rc) return rc;
+    b->key = key;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batches.push_front(b);
+    while (g_batches.size() > kMaxCached) { destroy_batch(g_batches.back()); g_batches.pop_back(); }
+  }
+  PC_CUDA(cudaGraphLaunch(b->exec, st));
+  if (dev_out)
+    for (int64_t i = 0; i < nq; ++i)
+      if (q[i].n_percolating)
+        PC_CUDA(cudaMemcpyAsync(q[i].n_percolating, b->qp[i].n_perc, 8, cudaMemcpyDeviceToDevice, st));
+  if (async) return PC_OK;
+  int err = 0;
+  if (b->plan) PC_CUDA(cudaMemcpyAsync(&err, stream_plan_error(b->plan), sizeof(int), cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned long long> cnt((size_t)nq);
+  for (int64_t i = 0; i < nq; ++i) {
+    const QueryPlan& P = b->qp[i];
+    PC_CUDA(cudaMemcpyAsync(&cnt[i], P.n_perc, 8, cudaMemcpyDeviceToHost, st));
+    if (!dev_out && q[i].n_configs > 0) {
+      const size_t n = (size_t)q[i].n_configs;
+      PC_CUDA(cudaMemcpyAsync(q[i].verdicts, P.v, n, cudaMemcpyDeviceToHost, st));
+      if (q[i].first_hit) PC_CUDA(cudaMemcpyAsync(q[i].first_hit, P.fh, 4 * n, cudaMemcpyDeviceToHost, st));
+      if (q[i].mass) PC_CUDA(cudaMemcpyAsync(q[i].mass, P.mass, 4 * n, cudaMemcpyDeviceToHost, st));
+      if (q[i].m_stop) PC_CUDA(cudaMemcpyAsync(q[i].m_stop, P.ms, 4 * n, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  PC_CUDA(cudaStreamSynchronize(st));
+  if (err) { set_error("streamed solver hit its tick bound"); return PC_ERR_INTERNAL; }
+  for (int64_t i = 0; i < nq; ++i) {
+    if (!dev_out && q[i].n_percolating) *q[i].n_percolating = (int64_t)cnt[i];
+    if (out) {
+      out[i].n_percolating = (int64_t)cnt[i];
+      out[i].Pi = q[i].n_configs ? (double)cnt[i] / (double)q[i].n_configs : 0.0;
+      out[i].solver = b->qp[i].solver;
+      out[i].threads = b->qp[i].threads;
+    }
+  }
+  return PC_OK;
+}

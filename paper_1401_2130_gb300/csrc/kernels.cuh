@@ -32,9 +32,18 @@ struct ResidentArgs {
 };
 size_t resident_smem(int A, int L);
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st);
+pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g,
+                            const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out);
+// default CTA size of the resident solver (about 16 tube layers per thread)
+int resident_threads(int A, int L);
+// CTA size picked by the autotuner for (W, L) (tune.cu); times candidates on a
+// miss, outside any stream capture
+int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st);
+bool resident_fits(int A, int L);
+void release_batches();
 
 // Streamed solver for lattices beyond shared memory, stream.cu.
-struct StreamJob {
+struct StreamQuery {
   Lattice lat;
   OccStream occ;
   const uint32_t* occ_bits;
@@ -43,6 +52,18 @@ struct StreamJob {
   uint32_t cfg0;
   Outputs out;
 };
+struct StreamJob : StreamQuery {
+  int* error_out = nullptr;  // device int: 1 if the tick bound was hit
+};
+struct StreamPlan;
+// Device resources for a set of queries (stream-ordered allocation on st).
+pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, StreamPlan** out);
+// Adds [init -> WHILE(sweep, control)] to g after deps; *last = the WHILE node.
+pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                          cudaGraphNode_t* last);
+int* stream_plan_error(StreamPlan* P);
+void stream_plan_release(StreamPlan* P, cudaStream_t st);
+size_t stream_slot_bytes(int A, int L);
 pc_status run_stream(const StreamJob& job, cudaStream_t st);
 
 // Standalone occupancy draw, occupancy.cu.

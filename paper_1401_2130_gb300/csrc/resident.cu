@@ -354,6 +354,51 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs P) {
   }
 }
 
+// Kernel, dynamic shared memory and grid of a resident launch.
+static pc_status resident_config(const ResidentArgs& args, int threads, void** func, size_t* smem,
+                                 long long* grid) {
+  if (args.lat.A > 32767) {
+    set_error("resident solver: more than 32767 columns");
+    return PC_ERR_OOM;
+  }
+  *smem = resident_smem_bytes(args.lat.A, args.lat.L);
+  const bool one = threads >= args.lat.A;
+  auto kern = one ? resident_kernel<true> : resident_kernel<false>;
+  PC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+  int dev = 0, nsm = 0, per_sm = 0;
+  PC_CUDA(cudaGetDevice(&dev));
+  PC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, *smem));
+  if (per_sm < 1) {
+    set_error("resident solver: lattice does not fit one CTA");
+    return PC_ERR_OOM;
+  }
+  long long g = (long long)per_sm * nsm;
+  if (g > args.n_cfg) g = args.n_cfg;
+  *grid = g;
+  *func = (void*)kern;
+  return PC_OK;
+}
+
+pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g,
+                            const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out) {
+  void* func = nullptr;
+  size_t smem = 0;
+  long long grid = 0;
+  pc_status rc = resident_config(args, threads, &func, &smem, &grid);
+  if (rc) return rc;
+  ResidentArgs a = args;
+  void* params[] = {&a};
+  cudaKernelNodeParams kp = {};
+  kp.func = func;
+  kp.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = params;
+  PC_CUDA(cudaGraphAddKernelNode(out, g, deps, ndeps, &kp));
+  return PC_OK;
+}
+
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st) {
   if (args.lat.A > 32767) {
     set_error("resident solver: more than 32767 columns");

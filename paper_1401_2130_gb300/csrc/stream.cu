@@ -1,22 +1,31 @@
 // stream.cu -- streamed solver for lattices whose state exceeds one CTA's
-// shared memory (Sec. II.B, Eqs. (2)-(4) on the lattice of Sec. II.A).
+// shared memory (Sec. II.B, Eqs. (2)-(4) on the lattice of Sec. II.A), for one
+// or many queries (W, L, p, seed, configuration range) at once.
 //
-// K "slots" each hold one configuration's state in HBM, laid out exactly as
-// the resident solver lays it out in shared memory (nu ping-pong rows t+1,
-// cf, occupancy and reached-set words [tw+1][a], column A an always-zero
-// sentinel).  The host replays a CUDA graph of "ticks"; each tick is
-//   sweep   : every CTA walks a global list of work units over all slots --
-//             FP32 site updates of step m over the causal window, the exact
-//             bit-parallel reached-set update, and lazy preparation of the
-//             layers just ahead of the window (Philox draw of a word row,
-//             1/deg rows, zeroing of nu and R rows);
-//   control : one CTA per slot reads the step's grow/end flags, sums the
+// K "slots" each hold one configuration's state in HBM:
+//   nu[2][(L+2) x S] FP32  nu = mu / deg (ping-pong, rows t+1, zero rows 0 and
+//                          L+1, column A an always-zero sentinel)
+//   dg[L x S]        u8    deg(i) for metallic sites (Eq. (2), detector edge
+//                          included on t = L-1), 0 for insulating ones
+//   occw, R[2]       bits  occupancy and reached set, words [tw+1][a] of 32
+//                          consecutive tube indices of column a
+// A slot takes configurations from a global work list (all queries, largest
+// lattices first) and is refilled as soon as its configuration finishes.
+// The device runs "ticks" inside one CUDA graph conditional WHILE node:
+//   sweep   : all CTAs walk a global list of work units over all slots --
+//             FP32 site updates of step m over the causal window t <= m, the
+//             exact bit-parallel reached-set update, and lazy preparation of
+//             the layers just ahead of the window (Philox draw of a word row,
+//             degrees, zeroing of nu and R rows);
+//   control : one CTA per slot reads the step's grow / end flags, sums the
 //             detector mass on a hit (deterministic block reduction), writes
-//             the configuration's outputs and refills the slot from the work
-//             counter (continuous refill: a slot never waits for the others).
-// The unit plan of a slot is a pure function of its control record, computed
-// identically by the sweep (to do the work) and by control (to advance G, F).
+//             the outputs, refills the slot and plans its next tick; the last
+//             CTA to finish prefix-sums the plans and sets the loop condition.
+// No host round trip between ticks; the loop ends when every configuration is
+// done or after a tick bound that no correct run reaches (then an error flag
+// is raised for the host).
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "common.cuh"
@@ -28,22 +37,12 @@ namespace {
 
 constexpr uint32_t kGrow = 1u, kEnd = 2u;
 enum : int { PH_EMPTY = 0, PH_DRAW0 = 1, PH_PREP0 = 2, PH_STEP = 3 };
-enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_KINDS = 4 };
-constexpr int kCols = 256;   // columns per unit == threads per sweep CTA
-constexpr int kRows = 16;    // layers (or word rows) per FP / BITS / PREP unit
-constexpr int kMaxSlots = 64;
+enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS = 5 };
+constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
+constexpr int kRows = 16;     // layers (or word rows) per FP / BITS / PREP unit
+constexpr int kMaxSlots = 1024;
 
-struct Ctl {
-  long long rel;       // relative configuration index in the slot
-  int phase;
-  int m;               // next step to compute (PH_STEP)
-  int G;               // layers with occupancy drawn (multiple of 32, or L)
-  int F;               // layers with cf computed and nu / R rows cleaned
-  unsigned int flags;  // grow / end of the step in flight
-  int pad;
-};
-
-struct Ctx {
+struct QDev {
   Lattice lat;
   OccStream occ;
   const uint32_t* occ_bits;
@@ -51,58 +50,108 @@ struct Ctx {
   int64_t n_cfg;
   uint32_t cfg0;
   Outputs out;
+  long long item0;  // first global work item of this query
+};
+
+struct __align__(16) Ctl {
+  long long item;       // global work item in the slot
+  int q;                // query of that item
+  int phase;
+  int m;                // step being computed (PH_STEP)
+  int G;                // layers with occupancy drawn (multiple of 32, or L)
+  int F;                // layers with degrees and cleaned nu / R rows
+  unsigned int flags;   // grow / end of the step in flight
+  int units[U_KINDS];   // this tick's units per kind
+};
+
+struct Ctx {
+  const QDev* qs;
+  int nq;
+  long long n_items;
   int K;
   Ctl* ctl;
-  float* nu;           // [K][2][(L+2)*S]
-  float* cf;           // [K][L*S]
-  uint32_t* occw;      // [K][TWP*S]
-  uint32_t* R;         // [K][2][TWP*S]
-  unsigned long long* work;
-  unsigned long long* n_done;
+  int* pre;                    // [K + 1] exclusive prefix of units over slots
+  char* pool;
+  size_t slot_bytes;
+  unsigned long long* work;    // next work item
+  unsigned long long* n_done;  // finished configurations
+  unsigned int* ticks;
+  unsigned int* arrive;        // control blocks finished this tick
+  int* error;
+  unsigned int max_ticks;
+  cudaGraphConditionalHandle cond;
 };
 
-// Segments of work for one slot in the tick that starts from record c.
 struct Plan {
-  int lo[U_KINDS], hi[U_KINDS];  // row ranges per kind (layers, or word rows for BITS/DRAW)
-  int G2, F2;                    // G and F after the tick
+  int lo[U_KINDS], hi[U_KINDS];
+  int G2, F2;
 };
 
-__host__ __device__ inline Plan make_plan(const Ctl& c, int L, int TW) {
+__host__ __device__ inline Plan make_plan(int phase, int m, int G, int F, int L, int TW) {
   Plan p;
   for (int k = 0; k < U_KINDS; ++k) { p.lo[k] = 0; p.hi[k] = 0; }
-  p.G2 = c.G; p.F2 = c.F;
-  if (c.phase == PH_DRAW0) {
+  p.G2 = G; p.F2 = F;
+  if (phase == PH_DRAW0) {
     const int rows = TW < 2 ? TW : 2;  // first 64 layers
-    p.lo[U_DRAW] = 0; p.hi[U_DRAW] = rows;
+    p.hi[U_DRAW] = rows;
     p.G2 = rows * 32 < L ? rows * 32 : L;
-  } else if (c.phase == PH_PREP0) {
-    p.lo[U_PREP] = 0; p.hi[U_PREP] = L < 5 ? L : 5;
+    // a slot may have held another lattice: zero the padding rows and the
+    // sentinel column of this one (one unit per column chunk)
+    p.hi[U_CLEAN] = 1;
+  } else if (phase == PH_PREP0) {
+    p.hi[U_PREP] = L < 5 ? L : 5;
     p.F2 = p.hi[U_PREP];
-  } else if (c.phase == PH_STEP) {
-    const int tmax = c.m < L - 1 ? c.m : L - 1;
-    p.lo[U_FP] = 0; p.hi[U_FP] = tmax + 1;
-    p.lo[U_BITS] = 0; p.hi[U_BITS] = (tmax >> 5) + 1;
-    // prepare two layers per tick (the window grows by one); occupancy of
-    // layer F2 must already be drawn: G >= min(F2 + 1, L)
-    int F2 = c.F + 2 < L ? c.F + 2 : L;
-    const int gneed = F2 + 1 < L ? F2 + 1 : L;
-    if (c.G < gneed) F2 = c.F;  // cannot happen with the draw rule below
-    p.lo[U_PREP] = c.F; p.hi[U_PREP] = F2;
+  } else if (phase == PH_STEP) {
+    const int tmax = m < L - 1 ? m : L - 1;
+    p.hi[U_FP] = tmax + 1;
+    p.hi[U_BITS] = (tmax >> 5) + 1;
+    // two layers prepared per tick (the window grows by one); the degrees of
+    // layer F2 - 1 need the occupancy of layer F2: G >= min(F2 + 1, L)
+    int F2 = F + 2 < L ? F + 2 : L;
+    if (G < (F2 + 1 < L ? F2 + 1 : L)) F2 = F;
+    p.lo[U_PREP] = F; p.hi[U_PREP] = F2;
     p.F2 = F2;
-    // keep occupancy one word row ahead of the prepared layers
-    if (c.G < L && c.G < F2 + 33) {
-      p.lo[U_DRAW] = c.G >> 5; p.hi[U_DRAW] = (c.G >> 5) + 1;
-      p.G2 = c.G + 32 < L ? c.G + 32 : L;
+    if (G < L && G < F2 + 33) {  // keep occupancy a word row ahead
+      p.lo[U_DRAW] = G >> 5; p.hi[U_DRAW] = (G >> 5) + 1;
+      p.G2 = G + 32 < L ? G + 32 : L;
     }
   }
   return p;
 }
 
-__device__ inline int n_units_of(int kind, int lo, int hi, int A) {
+__host__ __device__ inline int units_of(int kind, int lo, int hi, int A) {
   if (hi <= lo) return 0;
   const int ccol = (A + kCols - 1) / kCols;
-  const int rows_per = (kind == U_DRAW) ? 1 : kRows;
-  return ccol * ((hi - lo + rows_per - 1) / rows_per);
+  const int per = (kind == U_DRAW || kind == U_CLEAN) ? 1 : kRows;
+  return ccol * ((hi - lo + per - 1) / per);
+}
+
+// Sub-arrays of a slot for lattice lat.
+struct SlotView {
+  float* nu0; float* nu1; uint8_t* dg; uint32_t* occw; uint32_t* R0; uint32_t* R1;
+};
+
+__host__ __device__ inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__host__ __device__ inline size_t slot_bytes_of(int A, int L) {
+  const size_t S = (size_t)A + 1, TWP = (size_t)(L + 31) / 32 + 2;
+  return 2 * a256(sizeof(float) * (size_t)(L + 2) * S) + a256((size_t)L * S) +
+         3 * a256(sizeof(uint32_t) * TWP * S);
+}
+
+__device__ inline SlotView view_of(const Ctx& x, int slot, const Lattice& lat) {
+  const size_t S = (size_t)lat.S;
+  char* b = x.pool + (size_t)slot * x.slot_bytes;
+  SlotView v;
+  const size_t nu_b = a256(sizeof(float) * (size_t)(lat.L + 2) * S);
+  const size_t w_b = a256(sizeof(uint32_t) * (size_t)lat.TWP * S);
+  v.nu0 = (float*)b; b += nu_b;
+  v.nu1 = (float*)b; b += nu_b;
+  v.dg = (uint8_t*)b; b += a256((size_t)lat.L * S);
+  v.occw = (uint32_t*)b; b += w_b;
+  v.R0 = (uint32_t*)b; b += w_b;
+  v.R1 = (uint32_t*)b;
+  return v;
 }
 
 __device__ inline uint32_t bit_at(const uint32_t* w, int S, int col, int tt) {
@@ -116,56 +165,135 @@ __device__ inline uint32_t shifted_word(const uint32_t* R, int S, int col, int t
   return (w << 1) | (R[tw * S + col] >> 31);
 }
 
-__global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
-  __shared__ Ctl s_ctl[kMaxSlots];
-  __shared__ int s_pre[kMaxSlots * U_KINDS + 1];
-  __shared__ uint32_t s_flag;
-  const Lattice& lat = x.lat;
-  const int A = lat.A, L = lat.L, S = lat.S, TWP = lat.TWP;
-  const int tid = threadIdx.x;
-  const int K = x.K;
-  if (tid < K) s_ctl[tid] = x.ctl[tid];
-  __syncthreads();
-  if (tid < K) {
-    const Plan p = make_plan(s_ctl[tid], L, lat.TW);
-    for (int k = 0; k < U_KINDS; ++k) {
-      s_pre[tid * U_KINDS + k] = n_units_of(k, p.lo[k], p.hi[k], A);
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {  // exclusive prefix over (slot, kind)
-    int acc = 0;
-    for (int i = 0; i < K * U_KINDS; ++i) { const int v = s_pre[i]; s_pre[i] = acc; acc += v; }
-    s_pre[K * U_KINDS] = acc;
-  }
-  __syncthreads();
-  const int total = s_pre[K * U_KINDS];
-  const int ccol = (A + kCols - 1) / kCols;
-  const size_t nu_sz = (size_t)(L + 2) * S, w_sz = (size_t)TWP * S;
+// query of a global work item (queries are few; linear scan)
+__device__ inline int query_of(const Ctx& x, long long item) {
+  int q = 0;
+  while (q + 1 < x.nq && x.qs[q + 1].item0 <= item) ++q;
+  return q;
+}
 
+__device__ inline void fill_plan(Ctl& c, const Lattice& lat) {
+  const Plan p = make_plan(c.phase, c.m, c.G, c.F, lat.L, lat.TW);
+  for (int k = 0; k < U_KINDS; ++k) c.units[k] = units_of(k, p.lo[k], p.hi[k], lat.A);
+}
+
+__device__ inline void assign(const Ctx& x, Ctl& c, unsigned long long item) {
+  c.item = (long long)item; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
+  for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
+  if ((long long)item < x.n_items) {
+    c.q = query_of(x, (long long)item);
+    c.phase = PH_DRAW0;
+    fill_plan(c, x.qs[c.q].lat);
+  } else {
+    c.q = 0; c.phase = PH_EMPTY;
+  }
+}
+
+// exclusive prefix over slots of the unit totals, by one block
+__device__ void plan_prefix(const Ctx& x) {
+  __shared__ int s_part[32];
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int per = (x.K + T - 1) / T;
+  const int b0 = tid * per, b1 = min(b0 + per, x.K);
+  int sum = 0;
+  // other blocks wrote these records: read through L2, not a stale L1 line
+  for (int s = b0; s < b1; ++s) {
+    const int4 u = __ldcg((const int4*)x.ctl[s].units);
+    sum += u.x + u.y + u.z + u.w + __ldcg(&x.ctl[s].units[4]);
+  }
+  // block exclusive scan of per-thread sums (warp shuffles + 32 partials)
+  const int lane = tid & 31, warp = tid >> 5;
+  int v = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) s_part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < (T >> 5) ? s_part[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += n;
+    }
+    s_part[lane] = w;
+  }
+  __syncthreads();
+  int run = v - sum + (warp ? s_part[warp - 1] : 0);
+  for (int s = b0; s < b1; ++s) {
+    x.pre[s] = run;
+    const int4 u = __ldcg((const int4*)x.ctl[s].units);
+    run += u.x + u.y + u.z + u.w + __ldcg(&x.ctl[s].units[4]);
+  }
+  if (tid == T - 1) x.pre[x.K] = run;
+  __syncthreads();
+}
+
+// Query table upload through kernel parameters: asynchronous, and no
+// pageable host copy (which would synchronise the caller's stream).
+constexpr int kQChunk = 16;
+struct QChunk {
+  int n, base;
+  QDev q[kQChunk];
+};
+
+__global__ void upload_queries_kernel(QDev* dst, QChunk c) {
+  if ((int)threadIdx.x < c.n) dst[c.base + threadIdx.x] = c.q[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
+  for (int s = threadIdx.x; s < x.K; s += blockDim.x) {
+    Ctl c;
+    assign(x, c, (unsigned long long)s);
+    x.ctl[s] = c;
+  }
+  if (threadIdx.x == 0) {
+    *x.work = (unsigned long long)x.K;
+    *x.n_done = 0ull;
+    *x.ticks = 0u;
+    *x.arrive = 0u;
+    *x.error = 0;
+  }
+  __threadfence();
+  __syncthreads();
+  plan_prefix(x);
+}
+
+__global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
+  __shared__ float inv_deg[16];
+  __shared__ uint32_t s_flag;
+  const int tid = threadIdx.x;
+  if (tid < 16) inv_deg[tid] = tid ? __frcp_rn((float)tid) : 0.f;
+  __syncthreads();
+  const int total = x.pre[x.K];
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
-    // locate (slot, kind) by linear scan of the prefix
-    int idx = 0;
-    while (s_pre[idx + 1] <= u) ++idx;
-    const int slot = idx / U_KINDS, kind = idx % U_KINDS;
-    const int local = u - s_pre[idx];
+    // slot: last s with pre[s] <= u (binary search)
+    int lo = 0, hi = x.K - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (x.pre[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    const int slot = lo;
+    const Ctl c = x.ctl[slot];
+    int local = u - x.pre[slot], kind = 0;
+    while (local >= c.units[kind]) { local -= c.units[kind]; ++kind; }
+    const QDev& Q = x.qs[c.q];
+    const Lattice& lat = Q.lat;
+    const int A = lat.A, L = lat.L, S = lat.S;
+    const int ccol = (A + kCols - 1) / kCols;
     const int cchunk = local % ccol, rchunk = local / ccol;
     const int a = cchunk * kCols + tid;
-    const Ctl& c = s_ctl[slot];
-    float* nu0 = x.nu + (size_t)slot * 2 * nu_sz;
-    float* nu1 = nu0 + nu_sz;
-    float* cf = x.cf + (size_t)slot * L * S;
-    uint32_t* occw = x.occw + (size_t)slot * w_sz;
-    uint32_t* R0 = x.R + (size_t)slot * 2 * w_sz;
-    uint32_t* R1 = R0 + w_sz;
+    const Plan p = make_plan(c.phase, c.m, c.G, c.F, L, lat.TW);
+    const SlotView v = view_of(x, slot, lat);
 
     if (kind == U_FP) {
-      const Plan p = make_plan(c, L, lat.TW);
       const int t0 = p.lo[U_FP] + rchunk * kRows;
       const int t1 = min(t0 + kRows, p.hi[U_FP]);
-      const int m = c.m;
-      const float* __restrict__ src = (m & 1) ? nu0 : nu1;
-      float* __restrict__ dst = (m & 1) ? nu1 : nu0;
+      const bool odd = (c.m & 1) != 0;  // step m reads buffer (m-1)&1, writes m&1
+      const float* __restrict__ src = odd ? v.nu0 : v.nu1;
+      float* __restrict__ dst = odd ? v.nu1 : v.nu0;
       if (a < A) {
         const int sg = lat.sigma[a];
         int off[kLateral];
@@ -178,37 +306,34 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
           float s = below + above;
 #pragma unroll
           for (int d = 0; d < kLateral; ++d) s += src[base + off[d]];
-          dst[base + a] = cf[t * S + a] * s;
+          dst[base + a] = inv_deg[v.dg[t * S + a]] * s;
           below = here; here = above;
         }
       }
     } else if (kind == U_BITS) {
-      const Plan p = make_plan(c, L, lat.TW);
       const int w0 = p.lo[U_BITS] + rchunk * kRows;
       const int w1 = min(w0 + kRows, p.hi[U_BITS]);
-      const int m = c.m;
-      const int tmax = min(m, L - 1);
-      const uint32_t* Rs = (m & 1) ? R0 : R1;
-      uint32_t* Rd = (m & 1) ? R1 : R0;
+      const bool odd = (c.m & 1) != 0;
+      const uint32_t* Rs = odd ? v.R0 : v.R1;
+      uint32_t* Rd = odd ? v.R1 : v.R0;
       uint32_t fl = 0;
       if (a < A) {
         const int sg = lat.sigma[a];
-        int nb[kLateral], dt[kLateral];
+        int nb[kLateral];
 #pragma unroll
-        for (int d = 0; d < kLateral; ++d) { nb[d] = lat.nbr[a * kLateral + d]; dt[d] = dir_dt(d, sg); }
+        for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
         const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
         for (int tw = w0; tw < w1; ++tw) {
           uint32_t acc = shifted_word(Rs, S, a, tw, -1) | shifted_word(Rs, S, a, tw, 1);
 #pragma unroll
-          for (int d = 0; d < kLateral; ++d) acc |= shifted_word(Rs, S, nb[d], tw, dt[d]);
+          for (int d = 0; d < kLateral; ++d) acc |= shifted_word(Rs, S, nb[d], tw, dir_dt(d, sg));
           const int wi = (tw + 1) * S + a;
           const uint32_t old = Rs[wi];
-          const uint32_t nw = old | (acc & occw[wi]);
+          const uint32_t nw = old | (acc & v.occw[wi]);
           Rd[wi] = nw;
           if (nw != old) fl |= kGrow;
           if (tw == endw && (((nw & ~old) >> endb) & 1u)) fl |= kEnd;
         }
-        (void)tmax;
       }
       fl = __reduce_or_sync(0xffffffffu, fl);
       if (tid == 0) s_flag = 0u;
@@ -217,7 +342,6 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
       __syncthreads();
       if (tid == 0 && s_flag) atomicOr(&x.ctl[slot].flags, s_flag);
     } else if (kind == U_PREP) {
-      const Plan p = make_plan(c, L, lat.TW);
       const int t0 = p.lo[U_PREP] + rchunk * kRows;
       const int t1 = min(t0 + kRows, p.hi[U_PREP]);
       if (a < A) {
@@ -226,32 +350,44 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
 #pragma unroll
         for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
         for (int t = t0; t < t1; ++t) {
-          float cval = 0.f;
-          if (bit_at(occw, S, a, t)) {
-            int deg = (int)bit_at(occw, S, a, t - 1) + (int)bit_at(occw, S, a, t + 1) + (t == L - 1);
+          int deg = 0;
+          if (bit_at(v.occw, S, a, t)) {
+            deg = (int)bit_at(v.occw, S, a, t - 1) + (int)bit_at(v.occw, S, a, t + 1) + (t == L - 1);
 #pragma unroll
-            for (int d = 0; d < kLateral; ++d) deg += (int)bit_at(occw, S, nb[d], t + dir_dt(d, sg));
-            cval = deg ? __frcp_rn((float)deg) : 0.f;
+            for (int d = 0; d < kLateral; ++d) deg += (int)bit_at(v.occw, S, nb[d], t + dir_dt(d, sg));
           }
-          cf[t * S + a] = cval;
-          nu0[(t + 1) * S + a] = 0.f;
-          nu1[(t + 1) * S + a] = 0.f;
-          // reached-set word rows are cleaned one row ahead of the layers
-          if ((t & 31) == 0) {
-            const int wr = (t >> 5) + 2;  // data word row (t>>5)+1
-            R0[wr * S + a] = 0u; R1[wr * S + a] = 0u;
-            if (t == 0) { R0[S + a] = 0u; R1[S + a] = 0u; }
+          v.dg[t * S + a] = (uint8_t)deg;
+          v.nu0[(t + 1) * S + a] = 0.f;
+          v.nu1[(t + 1) * S + a] = 0.f;
+          if ((t & 31) == 0) {  // reached-set word rows cleaned one row ahead
+            const int wr = (t >> 5) + 2;
+            v.R0[wr * S + a] = 0u; v.R1[wr * S + a] = 0u;
+            if (t == 0) { v.R0[S + a] = 0u; v.R1[S + a] = 0u; }
           }
         }
       }
+    } else if (kind == U_CLEAN) {
+      // padding rows 0 and L+1 of nu, 0 and TW+1 of the bit arrays
+      if (a <= A) {
+        v.nu0[a] = 0.f; v.nu1[a] = 0.f;
+        v.nu0[(L + 1) * S + a] = 0.f; v.nu1[(L + 1) * S + a] = 0.f;
+        const int top = (lat.TW + 1) * S + a;
+        v.occw[a] = 0u; v.R0[a] = 0u; v.R1[a] = 0u;
+        v.occw[top] = 0u; v.R0[top] = 0u; v.R1[top] = 0u;
+      }
+      if (cchunk == 0) {  // the sentinel column A of every row
+        for (int r = tid; r < L + 2; r += kCols) { v.nu0[r * S + A] = 0.f; v.nu1[r * S + A] = 0.f; }
+        for (int r = tid; r < lat.TWP; r += kCols) {
+          v.occw[r * S + A] = 0u; v.R0[r * S + A] = 0u; v.R1[r * S + A] = 0u;
+        }
+      }
     } else {  // U_DRAW: one word row of occupancy, 32 tubes per word
-      const Plan p = make_plan(c, L, lat.TW);
       const int tw = p.lo[U_DRAW] + rchunk;
       if (a < A) {
+        const long long rel = c.item - Q.item0;
         uint32_t word = 0;
-        const uint32_t cfg = x.cfg0 + (uint32_t)c.rel;
-        if (x.occ_bits) {
-          const uint32_t* cb = x.occ_bits + (size_t)c.rel * x.words_per_cfg;
+        if (Q.occ_bits) {
+          const uint32_t* cb = Q.occ_bits + (size_t)rel * Q.words_per_cfg;
           for (int b = 0; b < 32; ++b) {
             const int t = tw * 32 + b;
             if (t >= L) break;
@@ -259,18 +395,17 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
             word |= ((cb[i >> 5] >> (i & 31)) & 1u) << b;
           }
         } else {
-          OccStream os = x.occ;
-          os.cfg = cfg;
+          const uint32_t cfg = Q.cfg0 + (uint32_t)rel;
           for (int b = 0; b < 32; ++b) {
             const int t = tw * 32 + b;
             if (t >= L) break;
             const int64_t i = (int64_t)t * A + a;
-            const u32x4 r = philox4x32_10(u32x4{(uint32_t)(i >> 2), cfg, os.wl, 0u}, os.k0, os.k1);
-            const uint32_t v = (i & 3) == 0 ? r.x : (i & 3) == 1 ? r.y : (i & 3) == 2 ? r.z : r.w;
-            word |= (uint32_t)((uint64_t)v < os.T) << b;
+            const u32x4 r = philox4x32_10(u32x4{(uint32_t)(i >> 2), cfg, Q.occ.wl, 0u}, Q.occ.k0, Q.occ.k1);
+            const uint32_t w = (i & 3) == 0 ? r.x : (i & 3) == 1 ? r.y : (i & 3) == 2 ? r.z : r.w;
+            word |= (uint32_t)((uint64_t)w < Q.occ.T) << b;
           }
         }
-        occw[(tw + 1) * S + a] = word;
+        v.occw[(tw + 1) * S + a] = word;
       }
     }
   }
@@ -296,189 +431,256 @@ __device__ inline float block_sum_f(float v, float* red) {
   return s;
 }
 
-// One CTA per slot.
+// One CTA per slot; the last CTA to finish plans the next tick.
 __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
   __shared__ float red[32];
   __shared__ int s_n0;
+  __shared__ bool s_last;
   const int slot = blockIdx.x, tid = threadIdx.x;
-  const Lattice& lat = x.lat;
-  const int A = lat.A, L = lat.L, S = lat.S;
-  const size_t nu_sz = (size_t)(L + 2) * S, w_sz = (size_t)lat.TWP * S;
   Ctl c = x.ctl[slot];
-  if (c.phase == PH_EMPTY) return;
-  float* nu0 = x.nu + (size_t)slot * 2 * nu_sz;
-  float* nu1 = nu0 + nu_sz;
-  const float* cf = x.cf + (size_t)slot * L * S;
-  const uint32_t* occw = x.occw + (size_t)slot * w_sz;
-  uint32_t* R0 = x.R + (size_t)slot * 2 * w_sz;
-
-  const Plan p = make_plan(c, L, lat.TW);
-  bool finish = false;
-  int verdict = 0, fh = -1, mstop = 0;
-  float mass = 0.f;
-  if (c.phase == PH_DRAW0) {
-    c.G = p.G2; c.phase = PH_PREP0;
-  } else if (c.phase == PH_PREP0) {
-    c.F = p.F2;
-    // m = 0: mu_0 uniform on the metallic sites of t = 0
-    if (tid == 0) s_n0 = 0;
-    __syncthreads();
-    int cnt = 0;
-    for (int a = tid; a < A; a += blockDim.x) cnt += (int)(occw[S + a] & 1u);
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if ((tid & 31) == 0 && cnt) atomicAdd(&s_n0, cnt);
-    __syncthreads();
-    const int n0 = s_n0;
-    if (n0 == 0) {
-      finish = true;
-    } else {
-      const float inv = __frcp_rn((float)n0);
-      float part = 0.f;
-      for (int a = tid; a < A; a += blockDim.x) {
-        const uint32_t b = occw[S + a] & 1u;
-        R0[S + a] = b;
-        const float v = b ? cf[a] * inv : 0.f;
-        nu0[S + a] = v;
-        part += v;
-      }
-      if (L == 1) {
-        mass = block_sum_f(part, red);
-        finish = true; verdict = 1; fh = 1; mstop = 1;
+  if (c.phase != PH_EMPTY) {
+    const QDev& Q = x.qs[c.q];
+    const Lattice& lat = Q.lat;
+    const int A = lat.A, L = lat.L, S = lat.S;
+    const SlotView v = view_of(x, slot, lat);
+    const Plan p = make_plan(c.phase, c.m, c.G, c.F, L, lat.TW);
+    bool finish = false;
+    int verdict = 0, fh = -1, mstop = 0;
+    float mass = 0.f;
+    if (c.phase == PH_DRAW0) {
+      c.G = p.G2; c.phase = PH_PREP0;
+    } else if (c.phase == PH_PREP0) {
+      c.F = p.F2;
+      // m = 0: mu_0 uniform on the metallic sites of t = 0
+      if (tid == 0) s_n0 = 0;
+      __syncthreads();
+      int cnt = 0;
+      for (int a = tid; a < A; a += blockDim.x) cnt += (int)(v.occw[S + a] & 1u);
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if ((tid & 31) == 0 && cnt) atomicAdd(&s_n0, cnt);
+      __syncthreads();
+      const int n0 = s_n0;
+      if (n0 == 0) {
+        finish = true;
       } else {
-        c.phase = PH_STEP; c.m = 1; c.flags = 0u;
+        const float inv = __frcp_rn((float)n0);
+        float part = 0.f;
+        for (int a = tid; a < A; a += blockDim.x) {
+          const uint32_t b = v.occw[S + a] & 1u;
+          v.R0[S + a] = b;
+          const int d = v.dg[a];
+          const float val = b ? (d ? __frcp_rn((float)d) : 0.f) * inv : 0.f;
+          v.nu0[S + a] = val;
+          part += val;
+        }
+        if (L == 1) {
+          mass = block_sum_f(part, red);
+          finish = true; verdict = 1; fh = 1; mstop = 1;
+        } else {
+          c.phase = PH_STEP; c.m = 1; c.flags = 0u;
+        }
+      }
+    } else if (c.phase == PH_STEP) {
+      c.G = p.G2; c.F = p.F2;
+      const unsigned f = c.flags;
+      c.flags = 0u;
+      if (f & kEnd) {
+        const float* dst = (c.m & 1) ? v.nu1 : v.nu0;
+        float part = 0.f;
+        for (int a = tid; a < A; a += blockDim.x) part += dst[L * S + a];
+        mass = block_sum_f(part, red);
+        finish = true; verdict = 1; fh = c.m + 1; mstop = c.m + 1;
+      } else if (!(f & kGrow)) {
+        finish = true; mstop = c.m;
+      } else {
+        c.m += 1;
       }
     }
-  } else if (c.phase == PH_STEP) {
-    c.G = p.G2; c.F = p.F2;
-    const unsigned f = c.flags;
-    c.flags = 0u;
-    if (f & kEnd) {
-      const float* dst = (c.m & 1) ? nu1 : nu0;
-      float part = 0.f;
-      for (int a = tid; a < A; a += blockDim.x) part += dst[L * S + a];
-      mass = block_sum_f(part, red);
-      finish = true; verdict = 1; fh = c.m + 1; mstop = c.m + 1;
-    } else if (!(f & kGrow)) {
-      finish = true; mstop = c.m;
-    } else {
-      c.m += 1;
-    }
-  }
-  if (finish) {
     if (tid == 0) {
-      const long long rel = c.rel;
-      x.out.verdict[rel] = (uint8_t)verdict;
-      if (x.out.first_hit) x.out.first_hit[rel] = fh;
-      if (x.out.mass) x.out.mass[rel] = mass;
-      if (x.out.m_stop) x.out.m_stop[rel] = mstop;
-      if (verdict && x.out.n_perc) atomicAdd(x.out.n_perc, 1ull);
-      atomicAdd(x.n_done, 1ull);
-      const unsigned long long nxt = atomicAdd(x.work, 1ull);
-      Ctl n;
-      n.rel = (long long)nxt; n.m = 0; n.G = 0; n.F = 0; n.flags = 0u; n.pad = 0;
-      n.phase = (long long)nxt < x.n_cfg ? PH_DRAW0 : PH_EMPTY;
-      x.ctl[slot] = n;
+      if (finish) {
+        const long long rel = c.item - Q.item0;
+        Q.out.verdict[rel] = (uint8_t)verdict;
+        if (Q.out.first_hit) Q.out.first_hit[rel] = fh;
+        if (Q.out.mass) Q.out.mass[rel] = mass;
+        if (Q.out.m_stop) Q.out.m_stop[rel] = mstop;
+        if (verdict && Q.out.n_perc) atomicAdd(Q.out.n_perc, 1ull);
+        atomicAdd(x.n_done, 1ull);
+        assign(x, c, atomicAdd(x.work, 1ull));
+      } else {
+        fill_plan(c, lat);
+      }
+      x.ctl[slot] = c;
     }
-  } else if (tid == 0) {
-    x.ctl[slot] = c;
   }
-}
-
-__global__ void init_slots_kernel(Ctx x) {
-  const int s = threadIdx.x;
-  if (s < x.K) {
-    Ctl n;
-    n.rel = s; n.m = 0; n.G = 0; n.F = 0; n.flags = 0u; n.pad = 0;
-    n.phase = s < x.n_cfg ? PH_DRAW0 : PH_EMPTY;
-    x.ctl[s] = n;
+  // last block: prefix of the next tick's units, loop condition
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(x.arrive, 1u) == (unsigned)(gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  plan_prefix(x);
+  if (tid == 0) {
+    *x.arrive = 0u;
+    const unsigned t = *x.ticks + 1u;
+    *x.ticks = t;
+    const bool more = *x.n_done < (unsigned long long)x.n_items;
+    if (more && t >= x.max_ticks) *x.error = 1;
+    cudaGraphSetConditional(x.cond, (more && t < x.max_ticks) ? 1u : 0u);
   }
-  if (s == 0) { *x.work = (unsigned long long)x.K; *x.n_done = 0ull; }
 }
 
 }  // namespace
 
-size_t stream_slot_bytes(int A, int L) {
-  const size_t S = (size_t)A + 1, TWP = (size_t)(L + 31) / 32 + 2;
-  return sizeof(float) * (2 * (size_t)(L + 2) * S + (size_t)L * S) + sizeof(uint32_t) * 3 * TWP * S;
-}
+size_t stream_slot_bytes(int A, int L) { return slot_bytes_of(A, L); }
 
-pc_status run_stream(const StreamJob& job, cudaStream_t st) {
-  if (job.n_cfg <= 0) return PC_OK;
-  const Lattice& lat = job.lat;
-  const size_t slot_bytes = stream_slot_bytes(lat.A, lat.L);
+struct StreamPlan {
+  Ctx x;
+  char* mem = nullptr;   // one allocation: queries, ctl, prefix, counters, pool
+  int grid = 0;
+  int* error_dev = nullptr;
+};
+
+pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, StreamPlan** out) {
+  *out = nullptr;
+  long long n_items = 0;
+  size_t slot = 0;
+  unsigned long long max_steps = 0;
+  std::vector<QDev> h(nq);
+  for (int i = 0; i < nq; ++i) {
+    h[i].lat = qs[i].lat; h[i].occ = qs[i].occ; h[i].occ_bits = qs[i].occ_bits;
+    h[i].words_per_cfg = qs[i].words_per_cfg; h[i].n_cfg = qs[i].n_cfg; h[i].cfg0 = qs[i].cfg0;
+    h[i].out = qs[i].out; h[i].item0 = n_items;
+    n_items += qs[i].n_cfg;
+    slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L));
+    max_steps = std::max<unsigned long long>(max_steps, (unsigned long long)qs[i].lat.N + 4);
+  }
   size_t free_b = 0, total_b = 0;
   PC_CUDA(cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = free_b / 2;
-  long long K = std::min<long long>(job.n_cfg, kMaxSlots);
-  K = std::min<long long>(K, (long long)(budget / (slot_bytes + 1)));
-  if (K < 1) {
+  long long K = std::min<long long>(n_items, kMaxSlots);
+  // PC_STREAM_MAX_SLOTS caps the pool (tests use it to force slot reuse)
+  if (const char* cap = std::getenv("PC_STREAM_MAX_SLOTS")) {
+    const long long c = std::atoll(cap);
+    if (c > 0) K = std::min<long long>(K, c);
+  }
+  K = std::min<long long>(K, (long long)(budget / (slot + 1)));
+  if (n_items > 0 && K < 1) {
     set_error("streamed solver: one configuration's state exceeds half the free device memory");
     return PC_ERR_OOM;
   }
-  Ctx x;
-  x.lat = lat; x.occ = job.occ; x.occ_bits = job.occ_bits; x.words_per_cfg = job.words_per_cfg;
-  x.n_cfg = job.n_cfg; x.cfg0 = job.cfg0; x.out = job.out; x.K = (int)K;
-  const size_t S = (size_t)lat.S, nu_sz = (size_t)(lat.L + 2) * S, w_sz = (size_t)lat.TWP * S;
-  char* pool = nullptr;
-  const size_t ctl_bytes = sizeof(Ctl) * kMaxSlots + 64;
-  const size_t pool_bytes = ctl_bytes + (size_t)K * slot_bytes + 256;
-  PC_CUDA(cudaMallocAsync((void**)&pool, pool_bytes, st));
-  pc_status rc = PC_OK;
-  unsigned long long* h_done = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  if (K < 1) K = 1;
+  const size_t hdr = a256(sizeof(QDev) * nq) + a256(sizeof(Ctl) * K) + a256(sizeof(int) * (K + 1)) + 256;
+  StreamPlan* P = new StreamPlan();
+  cudaError_t e = cudaMallocAsync((void**)&P->mem, hdr + (size_t)K * slot + 256, st);
+  if (e != cudaSuccess) { delete P; return cuda_fail(e, "stream plan alloc"); }
+  char* q = P->mem;
+  Ctx& x = P->x;
+  x.qs = (const QDev*)q; q += a256(sizeof(QDev) * nq);
+  x.nq = nq; x.n_items = n_items; x.K = (int)K;
+  x.ctl = (Ctl*)q; q += a256(sizeof(Ctl) * K);
+  x.pre = (int*)q; q += a256(sizeof(int) * (K + 1));
+  x.work = (unsigned long long*)q;
+  x.n_done = x.work + 1;
+  x.ticks = (unsigned int*)(x.work + 2);
+  x.arrive = x.ticks + 1;
+  x.error = (int*)(x.ticks + 2);
+  q += 256;
+  x.pool = q;
+  x.slot_bytes = slot;
+  // every configuration needs at most N + 3 ticks; slots run concurrently
+  const unsigned long long waves = (unsigned long long)((n_items + K - 1) / K);
+  const unsigned long long bound = waves * (max_steps + 4) + 64;
+  x.max_ticks = (unsigned int)std::min<unsigned long long>(bound, 0xffffff00ull);
+  P->error_dev = x.error;
+  for (int b = 0; b < nq && e == cudaSuccess; b += kQChunk) {
+    QChunk ch;
+    ch.base = b;
+    ch.n = std::min(kQChunk, nq - b);
+    for (int i = 0; i < ch.n; ++i) ch.q[i] = h[b + i];
+    upload_queries_kernel<<<1, kQChunk, 0, st>>>((QDev*)x.qs, ch);
+    e = cudaGetLastError();
+  }
+  // pool must start zeroed: padding rows / sentinel columns are never written
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.pool, 0, (size_t)K * slot, st);
+  if (e != cudaSuccess) { cudaFreeAsync(P->mem, st); delete P; return cuda_fail(e, "stream plan init"); }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  P->grid = nsm * 8;
+  *out = P;
+  return PC_OK;
+}
+
+// Adds [init kernel -> WHILE(sweep, control)] to graph g after deps.
+pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                          cudaGraphNode_t* last) {
+  Ctx& x = P->x;
+  PC_CUDA(cudaGraphConditionalHandleCreate(&x.cond, g, 1, cudaGraphCondAssignDefault));
+  void* args[] = {&x};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)stream_init_kernel;
+  kp.gridDim = dim3(1); kp.blockDim = dim3(1024); kp.sharedMemBytes = 0; kp.kernelParams = args;
+  cudaGraphNode_t n_init;
+  PC_CUDA(cudaGraphAddKernelNode(&n_init, g, deps, ndeps, &kp));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = x.cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t n_while;
+  PC_CUDA(cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaKernelNodeParams sp = {};
+  sp.func = (void*)sweep_kernel;
+  sp.gridDim = dim3(P->grid); sp.blockDim = dim3(kCols); sp.kernelParams = args;
+  cudaGraphNode_t n_sweep, n_ctl;
+  PC_CUDA(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &sp));
+  cudaKernelNodeParams cpk = {};
+  cpk.func = (void*)control_kernel;
+  cpk.gridDim = dim3(x.K); cpk.blockDim = dim3(kCols); cpk.kernelParams = args;
+  PC_CUDA(cudaGraphAddKernelNode(&n_ctl, body, &n_sweep, 1, &cpk));
+  *last = n_while;
+  return PC_OK;
+}
+
+int* stream_plan_error(StreamPlan* P) { return P->error_dev; }
+
+void stream_plan_release(StreamPlan* P, cudaStream_t st) {
+  if (!P) return;
+  if (P->mem) cudaFreeAsync(P->mem, st);
+  delete P;
+}
+
+// Single-query convenience used by pc_inspect: build, run, release (stream
+// ordered; no host synchronisation).
+pc_status run_stream(const StreamJob& job, cudaStream_t st) {
+  if (job.n_cfg <= 0) return PC_OK;
+  StreamQuery q;
+  q.lat = job.lat; q.occ = job.occ; q.occ_bits = job.occ_bits; q.words_per_cfg = job.words_per_cfg;
+  q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out;
+  StreamPlan* P = nullptr;
+  pc_status rc = stream_plan_create(&q, 1, st, &P);
+  if (rc) return rc;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
   do {
-    if (cudaMemsetAsync(pool, 0, pool_bytes, st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
-    char* q = pool;
-    x.ctl = (Ctl*)q; q += sizeof(Ctl) * kMaxSlots;
-    x.work = (unsigned long long*)q; q += 8;
-    x.n_done = (unsigned long long*)q; q += 56;
-    x.nu = (float*)q; q += sizeof(float) * K * 2 * nu_sz;
-    x.cf = (float*)q; q += sizeof(float) * K * lat.L * S;
-    x.occw = (uint32_t*)q; q += sizeof(uint32_t) * K * w_sz;
-    x.R = (uint32_t*)q;
-    init_slots_kernel<<<1, kMaxSlots, 0, st>>>(x);
-    if (cudaGetLastError() != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "init_slots"); break; }
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = nsm * 8;
-    // capture a chunk of ticks
-    const int ticks = 32;
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "stream"); break; }
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      for (int i = 0; i < ticks; ++i) {
-        sweep_kernel<<<grid, kCols, 0, cs>>>(x);
-        control_kernel<<<(unsigned)K, kCols, 0, cs>>>(x);
-      }
-      e = cudaStreamEndCapture(cs, &graph);
-    }
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) { rc = cuda_fail(e, "graph capture"); break; }
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "graph create"); break; }
+    cudaGraphNode_t last;
+    if ((rc = stream_plan_add(P, g, nullptr, 0, &last))) break;
+    e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) { rc = cuda_fail(e, "graph instantiate"); break; }
-    if (cudaMallocHost(&h_done, sizeof(unsigned long long)) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "host alloc"); break; }
-    *h_done = 0;
-    // Each configuration needs at most N + 3 ticks (the reached set grows by
-    // at least one site per step); bound the loop accordingly.
-    const long long max_replays = (long long)((job.n_cfg + K - 1) / K) * ((lat.N + 8) / ticks + 2) + 16;
-    long long replays = 0;
-    for (;;) {
-      e = cudaGraphLaunch(exec, st);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "graph launch"); break; }
-      e = cudaMemcpyAsync(h_done, x.n_done, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) { rc = cuda_fail(e, "poll"); break; }
-      if ((long long)*h_done >= job.n_cfg) break;
-      if (++replays > max_replays) { set_error("streamed solver did not converge"); rc = PC_ERR_INTERNAL; break; }
+    e = cudaGraphLaunch(ex, st);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "graph launch"); break; }
+    if (job.error_out) {
+      e = cudaMemcpyAsync(job.error_out, P->error_dev, sizeof(int), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "error copy"); break; }
     }
   } while (0);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (h_done) cudaFreeHost(h_done);
-  cudaFreeAsync(pool, st);
+  if (ex) cudaGraphExecDestroy(ex);  // an in-flight executable is freed on completion
+  if (g) cudaGraphDestroy(g);
+  stream_plan_release(P, st);
   return rc;
 }
 

@@ -1,0 +1,131 @@
+"""Batched submission (pc_batch_run): one CUDA graph for queries of mixed
+lattice sizes must give exactly the per-query results of pc_inspect and of
+the oracle, on first submission and on cached replays."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1401_2130_gb300 as pc
+
+pytestmark = pytest.mark.gpu
+
+MASS_TOL = 1e-5
+THREADS = os.cpu_count() or 1
+
+MIXED = [  # (W, L, p, seed, config_begin, n_configs)
+    (4, 16, 0.2, 5, 0, 500),      # resident
+    (8, 64, 0.19, 6, 100, 700),   # resident
+    (16, 64, 0.17, 7, 0, 150),    # streamed
+    (8, 128, 0.19, 8, 0, 200),    # streamed
+    (3, 40, 0.4, 9, 0, 200),      # resident
+    (0, 5, 0.9, 1, 0, 50),        # resident, single column
+    (2, 3, 0.0, 1, 0, 10),        # p = 0
+    (5, 7, 0.3, 2, 0, 0),         # empty query
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    pc.build()
+    pc.load()
+    torch.cuda.init()
+
+
+def _host(o):
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in o.items()}
+
+
+def _same(a, b, what):
+    for k in ("verdict", "first_hit", "m_stop"):
+        assert np.array_equal(np.asarray(a[k]).astype(np.int64), np.asarray(b[k]).astype(np.int64)), (what, k)
+    err = np.abs(np.asarray(a["mass"], np.float64) - np.asarray(b["mass"], np.float64))
+    assert err.max(initial=0.0) <= MASS_TOL, (what, err.max())
+
+
+def test_mixed_batch_equals_per_query_and_oracle():
+    outs, res = pc.pc_batch_run(MIXED)
+    kinds = [r["solver"] for r in res]
+    assert "resident" in kinds and "streamed" in kinds
+    for spec, o, r in zip(MIXED, outs, res):
+        W, L, p, seed, b, n = spec
+        ref = pc.pc_inspect(W, L, p, seed, b, n)
+        _same(o, ref, spec)
+        assert r["n_percolating"] == ref["n_percolating"]
+        if n:
+            orc = oracle.inspect(W, L, p=p, seed=seed, cfg0=b, n=n, mode="markov", threads=THREADS)
+            _same(o, orc, spec)
+
+
+def test_batch_replay_and_async_device_outputs():
+    import torch
+    queries, outs = pc.batch_queries(MIXED, device=True)
+    first = None
+    for rep in range(3):  # first call builds the graph, then replays
+        for o in outs:
+            o["verdict"].fill_(7)
+        s = torch.cuda.Stream()
+        pc.pc_batch_run(MIXED, device=True, async_=True, stream=s, outs=outs, queries=queries)
+        s.synchronize()
+        h = [_host(o) for o in outs]
+        if first is None:
+            first = h
+        for a, b, spec in zip(h, first, MIXED):
+            _same(a, b, spec)
+            for k in ("mass",):
+                assert np.array_equal(a[k], b[k])  # replay is bit-identical
+    for a, spec in zip(first, MIXED):
+        W, L, p, seed, b, n = spec
+        ref = pc.pc_inspect(W, L, p, seed, b, n)
+        _same(a, ref, spec)
+        assert int(a["n_percolating"][0]) == ref["n_percolating"]
+
+
+def test_slot_reuse_across_lattices(monkeypatch):
+    """Few slots, several streamed lattices of different shapes: every slot is
+    refilled many times with configurations of other lattices."""
+    monkeypatch.setenv("PC_STREAM_MAX_SLOTS", "3")
+    specs = [(16, 40, 0.3, 31, 0, 40), (9, 90, 0.25, 32, 0, 60), (12, 50, 0.28, 33, 0, 50),
+             (7, 200, 0.3, 34, 0, 40)]
+    outs, res = pc.pc_batch_run(specs)
+    assert all(r["solver"] == "streamed" for r in res)
+    for spec, o in zip(specs, outs):
+        W, L, p, seed, b, n = spec
+        ref = oracle.inspect(W, L, p=p, seed=seed, cfg0=b, n=n, mode="markov", threads=THREADS)
+        _same(o, ref, spec)
+
+
+def batching_workload(n=10_000):
+    """The finite-size-scaling batch: W in {4, 8, 16, 32} x L/W in {1, 2, ..., 64},
+    p = 0.1533, seed 3."""
+    return [(W, W * r, 0.1533, 3, 0, n) for W in (4, 8, 16, 32) for r in (1, 2, 4, 8, 16, 32, 64)]
+
+
+def test_batching_workload_full_size_sampled():
+    """The full 28-query batch in the benchmark's launch configuration (device
+    outputs, one graph); every configuration of the small lattices and a
+    sample of the large ones checked against the oracle."""
+    import torch
+    specs = batching_workload()
+    outs, res = pc.pc_batch_run(specs, device=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    for spec, o in zip(specs, outs):
+        W, L, p, seed, b, n = spec
+        h = _host(o)
+        A, N = oracle.lattice_info(W, L)
+        if N <= 20_000:
+            ref = oracle.inspect(W, L, p=p, seed=seed, n=n, mode="markov", threads=THREADS)
+            _same(h, ref, spec)
+        else:
+            k = 8 if N > 1_000_000 else 64
+            idx = np.sort(rng.choice(n, size=k, replace=False))
+            for i in idx:
+                r = oracle.inspect(W, L, p=p, seed=seed, cfg0=int(i), n=1, mode="bfs")
+                for key in ("verdict", "first_hit", "m_stop"):
+                    assert int(h[key][i]) == int(r[key][0]), (spec, int(i), key)
+        assert int(h["n_percolating"][0]) == int(h["verdict"].sum())
