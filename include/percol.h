@@ -164,6 +164,62 @@ pc_status pc_batch_run(const pc_query* queries, int64_t n_queries, pc_result* ou
                        int32_t flags, void* cuda_stream);
 
 /*
+ * Serving: a continuous-batching request loop on one device (the current
+ * device at pc_server_create).  Queries are admitted in arrival order as soon
+ * as their HBM footprint -- output buffers, plus the streamed solver's state
+ * for max(1, min(slots free, max_slots_per_query)) configurations when the
+ * lattice exceeds shared memory -- fits the server's device arena of
+ * hbm_budget_bytes.  Admitted queries run concurrently on the device:
+ * resident-size queries as persistent kernels on side streams, the others in
+ * the streamed solver's slots, which refill on the device while the query
+ * has configurations left.  New arrivals are admitted between chunks of
+ * ticks_per_poll device ticks.  Lattice state and occupancy counters stay on
+ * the device.  Each query's results equal pc_inspect's on the same query.
+ */
+typedef struct pc_server pc_server;
+
+typedef struct pc_server_opts {
+  uint64_t hbm_budget_bytes;   /* device arena (default 8 GiB) */
+  int32_t max_slots;           /* streamed-solver slots, 1..1024 (default 256) */
+  int32_t max_slots_per_query; /* cap per query (default 64) */
+  int32_t ticks_per_poll;      /* device ticks between admissions (default 8) */
+  int64_t max_pending;         /* queue bound; submit returns PC_ERR_BUSY beyond */
+} pc_server_opts;
+
+typedef struct pc_server_stats {
+  int64_t submitted, completed, configs_completed;
+  double p50_ms, p99_ms, mean_ms;  /* submit-to-completion latency */
+  double configs_per_s;            /* completed configurations / (last completion - first submission) */
+} pc_server_stats;
+
+/* opts may be NULL (defaults).  Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA. */
+pc_status pc_server_create(const pc_server_opts* opts, pc_server** out);
+
+/*
+ * Enqueue a query (n_configs >= 1).  Its output pointers are HOST pointers
+ * (optional), filled when the query completes.  Returns a ticket at once.
+ * Errors: PC_ERR_ARG, PC_ERR_OOM (footprint larger than the whole budget),
+ * PC_ERR_BUSY (queue full), PC_ERR_CANCELLED (server shutting down).
+ */
+pc_status pc_server_submit(pc_server* s, const pc_query* q, uint64_t* ticket);
+
+/*
+ * Wait up to timeout_ns (0: do not wait) for a ticket.  PC_OK fills out and
+ * retires the ticket; PC_ERR_BUSY if it is not finished yet (poll again);
+ * PC_ERR_CANCELLED if it was cancelled; PC_ERR_ARG for an unknown ticket.
+ */
+pc_status pc_server_poll(pc_server* s, uint64_t ticket, pc_result* out, int64_t timeout_ns);
+
+/* Cancel a ticket that has not been admitted yet (PC_ERR_BUSY if running). */
+pc_status pc_server_cancel(pc_server* s, uint64_t ticket);
+
+/* Latency percentiles and throughput of the completed queries so far. */
+pc_status pc_server_get_stats(pc_server* s, pc_server_stats* out);
+
+/* Stop the loop; pending tickets are cancelled; running work is drained. */
+pc_status pc_server_destroy(pc_server* s);
+
+/*
  * pc_inspect_static -- pc_inspect for callers that must not allocate device
  * memory.  The paper has no counterpart: this is a deployment variant of the
  * resident (shared-memory) solver.

@@ -43,6 +43,12 @@ SIGNATURES = {
     "pc_inspect_occupancy": [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_static": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pc_batch_run": [_vp, _i64, _vp, _i32, _vp],
+    "pc_server_create": [_vp, _vp],
+    "pc_server_submit": [_vp, _vp, _vp],
+    "pc_server_poll": [_vp, ctypes.c_uint64, _vp, _i64],
+    "pc_server_cancel": [_vp, ctypes.c_uint64],
+    "pc_server_get_stats": [_vp, _vp],
+    "pc_server_destroy": [_vp],
     "pc_shutdown": [],
     "pc_last_error": [],
 }
@@ -264,6 +270,101 @@ def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=No
             o["n_percolating"] = r["n_percolating"]
             o["Pi"] = r["Pi"]
     return outs, results
+
+
+class PcServerOpts(ctypes.Structure):
+    """Mirror of pc_server_opts."""
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("max_slots_per_query", ctypes.c_int32), ("ticks_per_poll", ctypes.c_int32),
+                ("max_pending", ctypes.c_int64)]
+
+
+class PcServerStats(ctypes.Structure):
+    """Mirror of pc_server_stats."""
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("configs_completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("configs_per_s", ctypes.c_double)]
+
+
+def pc_server_create(hbm_budget_bytes: int = 8 << 30, max_slots: int = 256,
+                     max_slots_per_query: int = 64, ticks_per_poll: int = 8,
+                     max_pending: int = 1 << 16) -> int:
+    """Create a serving loop on the current CUDA device; returns its handle."""
+    opts = PcServerOpts(hbm_budget_bytes, max_slots, max_slots_per_query, ticks_per_poll,
+                        max_pending)
+    h = ctypes.c_void_p()
+    _check(load().pc_server_create(ctypes.addressof(opts), ctypes.addressof(h)))
+    return h.value
+
+
+def pc_server_submit(handle: int, spec, outs: dict) -> int:
+    """Submit (W, L, p, seed, config_begin, n_configs); ``outs`` are host numpy
+    buffers (from _alloc_outputs) that must stay alive until the poll."""
+    W, L, p, seed, b, n = spec
+    q = PcQuery(W, L, float(p), int(seed) & (2**64 - 1), b, n, _ptr(outs["verdict"]),
+                _ptr(outs.get("first_hit")), _ptr(outs.get("mass")), _ptr(outs.get("m_stop")), None)
+    t = ctypes.c_uint64()
+    _check(load().pc_server_submit(handle, ctypes.addressof(q), ctypes.addressof(t)))
+    return t.value
+
+
+def pc_server_poll(handle: int, ticket: int, timeout_s: float = 0.0):
+    """Result dict once the ticket is done, None while it runs (PC_ERR_BUSY)."""
+    r = PcResult()
+    st = load().pc_server_poll(handle, ticket, ctypes.addressof(r), int(timeout_s * 1e9))
+    if st == PC_ERR_BUSY:
+        return None
+    _check(st)
+    return {"n_percolating": r.n_percolating, "Pi": r.Pi,
+            "solver": "resident" if r.solver == 0 else "streamed"}
+
+
+def pc_server_cancel(handle: int, ticket: int):
+    _check(load().pc_server_cancel(handle, ticket))
+
+
+def pc_server_get_stats(handle: int) -> dict:
+    st = PcServerStats()
+    _check(load().pc_server_get_stats(handle, ctypes.addressof(st)))
+    return {k: getattr(st, k) for k, _ in PcServerStats._fields_}
+
+
+def pc_server_destroy(handle: int):
+    _check(load().pc_server_destroy(handle))
+
+
+class Server:
+    """Convenience wrapper: keeps each submission's host outputs alive."""
+
+    def __init__(self, **opts):
+        self.handle = pc_server_create(**opts)
+        self.outs: dict[int, dict] = {}
+
+    def submit(self, spec) -> int:
+        o = _alloc_outputs(spec[5], False, ALL_OUTPUTS)
+        t = pc_server_submit(self.handle, spec, o)
+        self.outs[t] = o
+        return t
+
+    def poll(self, ticket: int, timeout_s: float = 0.0):
+        r = pc_server_poll(self.handle, ticket, timeout_s)
+        if r is None:
+            return None
+        o = self.outs.pop(ticket)
+        o.update(r)
+        return o
+
+    def cancel(self, ticket: int):
+        pc_server_cancel(self.handle, ticket)
+
+    def stats(self) -> dict:
+        return pc_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            pc_server_destroy(self.handle)
+            self.handle = None
 
 
 def pc_shutdown():

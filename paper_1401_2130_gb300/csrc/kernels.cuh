@@ -66,6 +66,19 @@ void stream_plan_release(StreamPlan* P, cudaStream_t st);
 size_t stream_slot_bytes(int A, int L);
 pc_status run_stream(const StreamJob& job, cudaStream_t st);
 
+// Server engine (stream.cu): streamed-solver slots bound to queries by the host.
+struct ServerEngine;
+pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk,
+                               cudaStream_t st, ServerEngine** out);
+void server_engine_destroy(ServerEngine* E);
+int server_engine_slots(const ServerEngine* E);
+pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& q, cudaStream_t st);
+pc_status server_engine_bind(ServerEngine* E, const int* slots, const int* queries, char* const* bases,
+                             int n, cudaStream_t st);
+pc_status server_engine_run_chunk(ServerEngine* E, cudaStream_t st);
+pc_status server_engine_status(ServerEngine* E, cudaStream_t st, const int** phases,
+                               const unsigned long long** qdone);
+
 // Standalone occupancy draw, occupancy.cu.
 pc_status launch_occupancy(const Lattice& lat, const OccStream& os, uint32_t cfg0,
                            int64_t n_cfg, uint32_t* occ_bits, cudaStream_t st);

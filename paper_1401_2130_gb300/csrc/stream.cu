@@ -80,6 +80,11 @@ struct Ctx {
   int* error;
   unsigned int max_ticks;
   cudaGraphConditionalHandle cond;
+  int use_cond;                 // set the WHILE condition at the end of a tick
+  int server;                   // 1: slots are bound to a query by the host
+  char** slot_base;             // [K] state of each slot (server mode)
+  unsigned long long* qnext;    // [nq] next configuration of a query (server mode)
+  unsigned long long* qdone;    // [nq] finished configurations (server mode)
 };
 
 struct Plan {
@@ -141,7 +146,7 @@ __host__ __device__ inline size_t slot_bytes_of(int A, int L) {
 
 __device__ inline SlotView view_of(const Ctx& x, int slot, const Lattice& lat) {
   const size_t S = (size_t)lat.S;
-  char* b = x.pool + (size_t)slot * x.slot_bytes;
+  char* b = x.server ? x.slot_base[slot] : x.pool + (size_t)slot * x.slot_bytes;
   SlotView v;
   const size_t nu_b = a256(sizeof(float) * (size_t)(lat.L + 2) * S);
   const size_t w_b = a256(sizeof(uint32_t) * (size_t)lat.TWP * S);
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
     } else {  // U_DRAW: one word row of occupancy, 32 tubes per word
       const int tw = p.lo[U_DRAW] + rchunk;
       if (a < A) {
-        const long long rel = c.item - Q.item0;
+        const long long rel = x.server ? c.item : c.item - Q.item0;
         uint32_t word = 0;
         if (Q.occ_bits) {
           const uint32_t* cb = Q.occ_bits + (size_t)rel * Q.words_per_cfg;
@@ -498,14 +503,25 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
     }
     if (tid == 0) {
       if (finish) {
-        const long long rel = c.item - Q.item0;
+        const long long rel = x.server ? c.item : c.item - Q.item0;
         Q.out.verdict[rel] = (uint8_t)verdict;
         if (Q.out.first_hit) Q.out.first_hit[rel] = fh;
         if (Q.out.mass) Q.out.mass[rel] = mass;
         if (Q.out.m_stop) Q.out.m_stop[rel] = mstop;
         if (verdict && Q.out.n_perc) atomicAdd(Q.out.n_perc, 1ull);
         atomicAdd(x.n_done, 1ull);
-        assign(x, c, atomicAdd(x.work, 1ull));
+        if (x.server) {
+          // the slot stays with its query while it has configurations left
+          atomicAdd(&x.qdone[c.q], 1ull);
+          const unsigned long long nxt = atomicAdd(&x.qnext[c.q], 1ull);
+          const int q = c.q;
+          c.item = (long long)nxt; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
+          for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
+          if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q].lat); }
+          else c.phase = PH_EMPTY;
+        } else {
+          assign(x, c, atomicAdd(x.work, 1ull));
+        }
       } else {
         fill_plan(c, lat);
       }
@@ -525,8 +541,10 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
     const unsigned t = *x.ticks + 1u;
     *x.ticks = t;
     const bool more = *x.n_done < (unsigned long long)x.n_items;
-    if (more && t >= x.max_ticks) *x.error = 1;
-    cudaGraphSetConditional(x.cond, (more && t < x.max_ticks) ? 1u : 0u);
+    if (x.use_cond) {
+      if (more && t >= x.max_ticks) *x.error = 1;
+      cudaGraphSetConditional(x.cond, (more && t < x.max_ticks) ? 1u : 0u);
+    }
   }
 }
 
@@ -588,6 +606,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   q += 256;
   x.pool = q;
   x.slot_bytes = slot;
+  x.use_cond = 0; x.server = 0; x.slot_base = nullptr; x.qnext = nullptr; x.qdone = nullptr;
   // every configuration needs at most N + 3 ticks; slots run concurrently
   const unsigned long long waves = (unsigned long long)((n_items + K - 1) / K);
   const unsigned long long bound = waves * (max_steps + 4) + 64;
@@ -617,6 +636,7 @@ pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* d
                           cudaGraphNode_t* last) {
   Ctx& x = P->x;
   PC_CUDA(cudaGraphConditionalHandleCreate(&x.cond, g, 1, cudaGraphCondAssignDefault));
+  x.use_cond = 1;
   void* args[] = {&x};
   cudaKernelNodeParams kp = {};
   kp.func = (void*)stream_init_kernel;
@@ -650,6 +670,187 @@ void stream_plan_release(StreamPlan* P, cudaStream_t st) {
   if (!P) return;
   if (P->mem) cudaFreeAsync(P->mem, st);
   delete P;
+}
+
+// ---------------------------------------------------------------------------
+// Server engine: the same ticks, with slots bound to queries by the host
+// (continuous batching).  The host uploads query entries, binds free slots to
+// admitted queries, runs chunks of ticks and reads back slot phases and
+// per-query completion counts between chunks.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kBindChunk = 64;
+struct BindList {
+  int n;
+  int slot[kBindChunk];
+  int query[kBindChunk];
+  char* base[kBindChunk];
+};
+
+__global__ void __launch_bounds__(1024) server_bind_kernel(Ctx x, BindList b) {
+  if ((int)threadIdx.x < b.n) {
+    const int s = b.slot[threadIdx.x], q = b.query[threadIdx.x];
+    x.slot_base[s] = b.base[threadIdx.x];
+    Ctl c;
+    const unsigned long long nxt = atomicAdd(&x.qnext[q], 1ull);
+    c.item = (long long)nxt; c.q = q; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
+    for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
+    if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q].lat); }
+    else c.phase = PH_EMPTY;
+    x.ctl[s] = c;
+  }
+  __threadfence();
+  __syncthreads();
+  plan_prefix(x);
+}
+
+__global__ void server_reset_kernel(Ctx x) {
+  for (int s = threadIdx.x; s < x.K; s += blockDim.x) {
+    Ctl c;
+    c.item = 0; c.q = 0; c.phase = PH_EMPTY; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
+    for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
+    x.ctl[s] = c;
+    x.pre[s] = 0;
+  }
+  if (threadIdx.x == 0) { x.pre[x.K] = 0; *x.arrive = 0u; *x.ticks = 0u; *x.n_done = 0ull; }
+}
+
+__global__ void server_status_kernel(Ctx x, int* phases) {
+  for (int s = threadIdx.x; s < x.K; s += blockDim.x) phases[s] = x.ctl[s].phase;
+}
+
+}  // namespace
+
+struct ServerEngine {
+  Ctx x;
+  char* mem = nullptr;
+  int* d_phase = nullptr;
+  int* h_phase = nullptr;                 // pinned [K]
+  unsigned long long* h_qdone = nullptr;  // pinned [nq]
+  cudaGraphExec_t chunk = nullptr;
+  int max_queries = 0;
+};
+
+pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk,
+                               cudaStream_t st, ServerEngine** out) {
+  *out = nullptr;
+  ServerEngine* E = new ServerEngine();
+  Ctx& x = E->x;
+  const int K = std::max(1, std::min(max_slots, kMaxSlots));
+  const int nq = std::max(1, max_queries);
+  const size_t bytes = a256(sizeof(QDev) * nq) + a256(sizeof(Ctl) * K) + a256(sizeof(int) * (K + 1)) +
+                       a256(sizeof(char*) * K) + 2 * a256(sizeof(unsigned long long) * nq) +
+                       a256(sizeof(int) * K) + 256;
+  cudaError_t e = cudaMalloc((void**)&E->mem, bytes);
+  if (e != cudaSuccess) { delete E; return cuda_fail(e, "server engine alloc"); }
+  char* q = E->mem;
+  x = Ctx{};
+  x.qs = (const QDev*)q; q += a256(sizeof(QDev) * nq);
+  x.nq = nq; x.n_items = 0; x.K = K;
+  x.ctl = (Ctl*)q; q += a256(sizeof(Ctl) * K);
+  x.pre = (int*)q; q += a256(sizeof(int) * (K + 1));
+  x.slot_base = (char**)q; q += a256(sizeof(char*) * K);
+  x.qnext = (unsigned long long*)q; q += a256(sizeof(unsigned long long) * nq);
+  x.qdone = (unsigned long long*)q; q += a256(sizeof(unsigned long long) * nq);
+  E->d_phase = (int*)q; q += a256(sizeof(int) * K);
+  x.work = (unsigned long long*)q;
+  x.n_done = x.work + 1;
+  x.ticks = (unsigned int*)(x.work + 2);
+  x.arrive = x.ticks + 1;
+  x.error = (int*)(x.ticks + 2);
+  x.pool = nullptr; x.slot_bytes = 0; x.max_ticks = 0xffffffffu;
+  x.use_cond = 0; x.server = 1;
+  E->max_queries = nq;
+  pc_status rc = PC_OK;
+  do {
+    if ((e = cudaMemsetAsync(E->mem, 0, bytes, st)) != cudaSuccess) { rc = cuda_fail(e, "server memset"); break; }
+    server_reset_kernel<<<1, 1024, 0, st>>>(x);
+    if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "server reset"); break; }
+    if ((e = cudaMallocHost((void**)&E->h_phase, sizeof(int) * K)) != cudaSuccess) { rc = cuda_fail(e, "pinned"); break; }
+    if ((e = cudaMallocHost((void**)&E->h_qdone, sizeof(unsigned long long) * nq)) != cudaSuccess) { rc = cuda_fail(e, "pinned"); break; }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaGraph_t g;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) { rc = cuda_fail(e, "graph"); break; }
+    void* args[] = {&x};
+    cudaGraphNode_t prev = nullptr;
+    for (int t = 0; t < std::max(1, ticks_per_chunk) && rc == PC_OK; ++t) {
+      cudaKernelNodeParams sp = {};
+      sp.func = (void*)sweep_kernel; sp.gridDim = dim3(nsm * 8); sp.blockDim = dim3(kCols);
+      sp.kernelParams = args;
+      cudaGraphNode_t ns, nc;
+      if ((e = cudaGraphAddKernelNode(&ns, g, prev ? &prev : nullptr, prev ? 1 : 0, &sp)) != cudaSuccess) { rc = cuda_fail(e, "node"); break; }
+      cudaKernelNodeParams cp = {};
+      cp.func = (void*)control_kernel; cp.gridDim = dim3(K); cp.blockDim = dim3(kCols);
+      cp.kernelParams = args;
+      if ((e = cudaGraphAddKernelNode(&nc, g, &ns, 1, &cp)) != cudaSuccess) { rc = cuda_fail(e, "node"); break; }
+      prev = nc;
+    }
+    if (rc == PC_OK && (e = cudaGraphInstantiate(&E->chunk, g, 0)) != cudaSuccess) rc = cuda_fail(e, "instantiate");
+    cudaGraphDestroy(g);
+    if (rc == PC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) rc = cuda_fail(e, "server init sync");
+  } while (0);
+  if (rc) { server_engine_destroy(E); return rc; }
+  *out = E;
+  return PC_OK;
+}
+
+void server_engine_destroy(ServerEngine* E) {
+  if (!E) return;
+  if (E->chunk) cudaGraphExecDestroy(E->chunk);
+  if (E->h_phase) cudaFreeHost(E->h_phase);
+  if (E->h_qdone) cudaFreeHost(E->h_qdone);
+  if (E->mem) cudaFree(E->mem);
+  delete E;
+}
+
+int server_engine_slots(const ServerEngine* E) { return E->x.K; }
+
+pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& sq, cudaStream_t st) {
+  if (qi < 0 || qi >= E->max_queries) { set_error("server: query index out of range"); return PC_ERR_ARG; }
+  QChunk ch;
+  ch.base = qi; ch.n = 1;
+  QDev& d = ch.q[0];
+  d.lat = sq.lat; d.occ = sq.occ; d.occ_bits = sq.occ_bits; d.words_per_cfg = sq.words_per_cfg;
+  d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0;
+  upload_queries_kernel<<<1, kQChunk, 0, st>>>((QDev*)E->x.qs, ch);
+  PC_CUDA(cudaGetLastError());
+  PC_CUDA(cudaMemsetAsync(E->x.qnext + qi, 0, sizeof(unsigned long long), st));
+  PC_CUDA(cudaMemsetAsync(E->x.qdone + qi, 0, sizeof(unsigned long long), st));
+  return PC_OK;
+}
+
+pc_status server_engine_bind(ServerEngine* E, const int* slots, const int* queries, char* const* bases,
+                             int n, cudaStream_t st) {
+  for (int b = 0; b < n; b += kBindChunk) {
+    BindList bl;
+    bl.n = std::min(kBindChunk, n - b);
+    for (int i = 0; i < bl.n; ++i) { bl.slot[i] = slots[b + i]; bl.query[i] = queries[b + i]; bl.base[i] = bases[b + i]; }
+    server_bind_kernel<<<1, 1024, 0, st>>>(E->x, bl);
+    PC_CUDA(cudaGetLastError());
+  }
+  return PC_OK;
+}
+
+pc_status server_engine_run_chunk(ServerEngine* E, cudaStream_t st) {
+  PC_CUDA(cudaGraphLaunch(E->chunk, st));
+  return PC_OK;
+}
+
+// Enqueue the copy of slot phases and per-query completion counts to pinned
+// host memory; valid after st reaches this point.
+pc_status server_engine_status(ServerEngine* E, cudaStream_t st, const int** phases,
+                               const unsigned long long** qdone) {
+  server_status_kernel<<<1, 1024, 0, st>>>(E->x, E->d_phase);
+  PC_CUDA(cudaGetLastError());
+  PC_CUDA(cudaMemcpyAsync(E->h_phase, E->d_phase, sizeof(int) * E->x.K, cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(E->h_qdone, E->x.qdone, sizeof(unsigned long long) * E->max_queries,
+                          cudaMemcpyDeviceToHost, st));
+  *phases = E->h_phase;
+  *qdone = E->h_qdone;
+  return PC_OK;
 }
 
 // Single-query convenience used by pc_inspect: build, run, release (stream
