@@ -290,6 +290,93 @@ def run_batch(args, pc, torch):
     }
 
 
+def serving_specs(n_queries: int, seed: int = 5):
+    """The serving query stream (seed 5): W ~ U{4..64}, L = round(W e^U(0, ln 64)),
+    p ~ U[0.12, 0.19], n_configs = round(e^U(ln 100, ln 10^4)); the first
+    n_queries queries, and the Poisson arrival gaps (unit rate) of the stream."""
+    rng = np.random.default_rng(seed)
+    specs, gaps = [], []
+    for i in range(n_queries):
+        W_ = int(rng.integers(4, 65))
+        L_ = int(round(W_ * np.exp(rng.uniform(0.0, np.log(64.0)))))
+        p_ = float(rng.uniform(0.12, 0.19))
+        n_ = int(round(np.exp(rng.uniform(np.log(100.0), np.log(1e4)))))
+        specs.append((W_, max(L_, 1), p_, seed, 0, n_))
+    arr = np.random.default_rng(seed + 1000)
+    gaps = arr.exponential(1.0, size=n_queries)
+    return specs, gaps
+
+
+def run_serving(args, pc, torch):
+    specs, gaps = serving_specs(args.serve_queries)
+    n_tot = sum(sp[5] for sp in specs)
+    # plain: one query after another through pc_inspect
+    for sp in specs[:2]:
+        pc.pc_inspect(*sp)
+    torch.cuda.synchronize()
+    svc, plain = [], []
+    for sp in specs:
+        t0 = time.perf_counter()
+        plain.append(pc.pc_inspect(*sp))
+        svc.append(time.perf_counter() - t0)
+    t_plain = float(sum(svc))
+    opts = dict(hbm_budget_bytes=args.serve_budget_gb << 30, max_slots=512, max_slots_per_query=128,
+                ticks_per_poll=8)
+
+    def serve(arrivals):
+        srv = pc.Server(**opts)
+        try:
+            t0 = time.perf_counter()
+            tickets = []
+            for sp, ta in zip(specs, arrivals):
+                while time.perf_counter() - t0 < ta:
+                    time.sleep(min(0.001, ta - (time.perf_counter() - t0)))
+                tickets.append(srv.submit(sp))
+            res = {}
+            while len(res) < len(tickets):
+                for t in tickets:
+                    if t not in res:
+                        r = srv.poll(t, timeout_s=0.002)
+                        if r is not None:
+                            res[t] = r
+            st = srv.stats()
+        finally:
+            srv.close()
+        return [res[t] for t in tickets], st
+
+    with Clocks(0) as clk:
+        sat, st_sat = serve([0.0] * len(specs))
+        lam = 0.7 * len(specs) / t_plain  # queries per second at 70% of plain capacity
+        arrivals = np.cumsum(gaps) / lam
+        arrivals -= arrivals[0]
+        _, st_open = serve(list(arrivals))
+    same = all(np.array_equal(a["verdict"], b["verdict"]) and np.array_equal(a["first_hit"], b["first_hit"])
+               and np.array_equal(a["m_stop"], b["m_stop"]) for a, b in zip(sat, plain))
+    # a plain FIFO server on the same arrivals with the measured service times
+    t_free, lat = 0.0, []
+    for ta, sv in zip(arrivals, svc):
+        start = max(ta, t_free)
+        t_free = start + sv
+        lat.append((t_free - ta) * 1e3)
+    lat = np.sort(np.array(lat))
+    pq = lambda a, f: float(a[min(len(a) - 1, int(round(f * (len(a) - 1))))])
+    return {
+        "metric": "configs/s (served)", "value": st_sat["configs_per_s"], "unit": "configs/s",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": n_tot / st_sat["configs_per_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"serving stream seed=5, first {len(specs)} queries "
+                               f"({n_tot} configurations)", "server": opts,
+                   "arrival_rate_qps": lam, "l2": "n/a (mixed working sets)"},
+        "plain_configs_per_s": n_tot / t_plain, "served_over_plain": t_plain * st_sat["configs_per_s"] / n_tot,
+        "open_loop": {"p50_ms": st_open["p50_ms"], "p99_ms": st_open["p99_ms"],
+                      "mean_ms": st_open["mean_ms"], "configs_per_s": st_open["configs_per_s"]},
+        "plain_fifo_same_arrivals": {"p50_ms": pq(lat, 0.5), "p99_ms": pq(lat, 0.99)},
+        "saturation_latency": {"p50_ms": st_sat["p50_ms"], "p99_ms": st_sat["p99_ms"]},
+        "results_identical": bool(same), "clocks": clk.summary(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,7 +388,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--configs-per-p", type=int, default=N_CFG,
                     help="smaller cases for profiling only; the benchmark workload is 10^4")
-    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch"])
+    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch", "serving"])
+    ap.add_argument("--serve-queries", type=int, default=24)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--large-configs", type=int, default=64)
     ap.add_argument("--batch-configs", type=int, default=10_000)
     args = ap.parse_args()
@@ -313,7 +402,7 @@ def main():
         torch.cuda.set_device(0)
         pc.build()
         pc.load()
-        fn = run_large if args.workload == "large" else run_batch
+        fn = {"large": run_large, "batch": run_batch, "serving": run_serving}[args.workload]
         print(json.dumps(fn(args, pc, torch)), flush=True)
         return 0
 
@@ -419,6 +508,7 @@ def main():
         "e2e": {"value": su_step * world / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": len(PS) * args.steps,
+        "per_p_ms": [float(np.mean(launch_ms[i::len(PS)])) for i in range(len(PS))],
         "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -229,7 +229,7 @@ pc_status pc_server_destroy(pc_server* s);
  * and latency-critical loops that cannot afford cudaMalloc / cudaFree, which
  * may synchronise the whole device.  This call performs no device allocation
  * of any kind: its scratch (counters, lattice tables, device staging of the
- * outputs) is one static device array of about 3.8 MB that every GPU loading
+ * outputs) is one static device array of about 3.9 MB that every GPU loading
  * the library holds until the process exits.
  *
  * Arguments and outputs as pc_inspect with host outputs (all output pointers
@@ -252,6 +252,21 @@ pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t seed,
                             uint8_t* verdicts, int32_t* first_hit, float* mass,
                             int32_t* m_stop, int64_t* n_percolating, double* Pi,
                             void* cuda_stream);
+
+/*
+ * Plane layout used by the solvers for per-layer FP arrays (diagnostics and
+ * tests; host only).  Rows of the hexagon are stored in order with 2-4 zero
+ * entries before each, so that plane position mod 3 equals the column's
+ * sublattice, followed by a zero zone that stands for the rows outside the
+ * hexagon.  Outputs: P (entries per plane), the strips [s_begin, s_begin +
+ * n_strips) (strip s = positions 3s..3s+2), strip_row [n_strips] (row index
+ * 0..2W of each strip), row_off [(2W+1) x 4] (offset from a column of row r
+ * to the same q in rows r-2, r-1, r+1, r+2), ppos [A] (position of each
+ * column), pcol [P] (column at each position, -1 for zeros).  Query P and
+ * n_strips first with NULL arrays.  Errors: PC_ERR_ARG.
+ */
+pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
+                            int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol);
 
 /* Release cached lattice tables and scratch of every device. */
 pc_status pc_shutdown(void);

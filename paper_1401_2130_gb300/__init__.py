@@ -49,6 +49,7 @@ SIGNATURES = {
     "pc_server_cancel": [_vp, ctypes.c_uint64],
     "pc_server_get_stats": [_vp, _vp],
     "pc_server_destroy": [_vp],
+    "pc_lattice_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
 }
@@ -114,6 +115,20 @@ def pc_lattice_info(W: int, L: int) -> tuple[int, int]:
     a = ctypes.c_int64(); n = ctypes.c_int64()
     _check(load().pc_lattice_info(W, L, ctypes.byref(a), ctypes.byref(n)))
     return a.value, n.value
+
+
+def pc_lattice_layout(W: int) -> dict:
+    """Plane layout of radius W used by the FP arrays (see percol.h)."""
+    lib = load()
+    P, sb, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.pc_lattice_layout(W, ctypes.addressof(P), ctypes.addressof(sb), ctypes.addressof(ns),
+                                 None, None, None, None))
+    A = 3 * W * (W + 1) + 1
+    sr = np.zeros(ns.value, np.int16); ro = np.zeros((2 * W + 1, 4), np.int32)
+    pp = np.zeros(A, np.int32); pcl = np.zeros(P.value, np.int32)
+    _check(lib.pc_lattice_layout(W, None, None, None, _ptr(sr), _ptr(ro), _ptr(pp), _ptr(pcl)))
+    return {"P": P.value, "s_begin": sb.value, "n_strips": ns.value, "strip_row": sr,
+            "row_off": ro, "ppos": pp, "pcol": pcl}
 
 
 def words_per_config(W: int, L: int) -> int:

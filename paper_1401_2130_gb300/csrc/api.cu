@@ -46,19 +46,24 @@ pc_status check_range(int64_t config_begin, int64_t n_configs) {
 
 }  // namespace
 
-bool resident_fits(int A, int L) {
+bool resident_fits(int W, int L) {
   int dev = 0, max_smem = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return A <= 32767 && resident_smem(A, L) <= (size_t)max_smem;
+  const int64_t A = n_columns(W);
+  if (A > 32767) return false;
+  Lattice lat = {};
+  lat.W = W; lat.L = L; lat.A = (int)A;
+  layout_fill(W, &lat.P, &lat.s_begin, &lat.n_strips, nullptr, nullptr, nullptr, nullptr);
+  return resident_smem(lat) <= (size_t)max_smem;
 }
 
 int resident_threads(int A, int L) {
-  const int per = (L + 15) / 16;  // aim at ~16 tube layers per thread
-  long long t = (long long)A * per;
-  t = (t + 31) / 32 * 32;
+  // about one (strip, 16-layer chunk) item per thread; strips ~ A / 3
+  const long long items = ((long long)A / 3 + 1) * ((L + 15) / 16);
+  long long t = (items + 31) / 32 * 32;
   if (t < 128) t = 128;
-  if (t > 1024) t = 1024;
+  if (t > 640) t = 640;
   return (int)t;
 }
 
@@ -131,11 +136,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
     os.T = occ_bits ? 0 : threshold_of(p);
     const int64_t wpc = (lat.N + 31) / 32;
 
-    int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = resident_smem(lat.A, lat.L);
-    bool resident = need <= (size_t)max_smem;
+    bool resident = resident_fits(W, L);
     if (flags & PC_MODE_STREAM) resident = false;
     if ((flags & PC_MODE_RESIDENT) && !resident) {
       set_error("PC_MODE_RESIDENT: lattice state exceeds shared memory"); rc = PC_ERR_OOM; break;
@@ -146,7 +147,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       a.n_cfg = n; a.cfg0 = (uint32_t)cfg0;
       a.verdict = s.verdict; a.first_hit = s.first_hit; a.mass = s.mass; a.m_stop = s.m_stop;
       a.n_perc = s.n_perc; a.work = s.work; a.prep_chunk = 8;
-      rc = launch_resident(a, resident_threads(lat.A, lat.L), st);
+      rc = launch_resident(a, tuned_threads(lat, occ_bits ? 0.2 : p, seed, st), st);
     } else {
       StreamJob j;
       j.lat = lat; j.occ = os; j.occ_bits = occ_bits; j.words_per_cfg = wpc;
@@ -168,7 +169,8 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       if (e == cudaSuccess) e = cudaMemcpyAsync(&err, s.work + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) { rc = cuda_fail(e, "copy outputs"); break; }
-      if (err) { set_error("streamed solver hit its tick bound"); rc = PC_ERR_INTERNAL; break; }
+      if (err & 2) { set_error("streamed solver: a bulk-copy wait timed out"); rc = PC_ERR_TIMEOUT; break; }
+      if (err) { set_error("streamed solver: tick bound or segment check failed"); rc = PC_ERR_INTERNAL; break; }
       if (n_percolating) *n_percolating = (int64_t)cnt;
       if (Pi) *Pi = (double)cnt / (double)n;
     }

@@ -85,7 +85,7 @@ int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st) 
   cudaEventCreate(&e1);
   int best = fallback;
   float best_ms = 1e30f;
-  const int cand[] = {128, 256, 384, 512, 768, 1024};
+  const int cand[] = {128, 256, 384, 512, 640};
   for (int T : cand) {
     ResidentArgs a;
     a.lat = lat;
@@ -208,7 +208,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
       OccStream os;
       os.k0 = (uint32_t)(q[i].seed & 0xffffffffu); os.k1 = (uint32_t)(q[i].seed >> 32);
       os.cfg = 0; os.wl = (uint32_t)q[i].W | ((uint32_t)q[i].L << 8); os.T = threshold_of(q[i].p);
-      if (resident_fits(lat.A, lat.L)) {
+      if (resident_fits(q[i].W, q[i].L)) {
         P.solver = 0;
         P.threads = tuned_threads(lat, q[i].p, q[i].seed, st);
         ResidentArgs a;
@@ -317,7 +317,8 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
     }
   }
   PC_CUDA(cudaStreamSynchronize(st));
-  if (err) { set_error("streamed solver hit its tick bound"); return PC_ERR_INTERNAL; }
+  if (err & 2) { set_error("streamed solver: a bulk-copy wait timed out"); return PC_ERR_TIMEOUT; }
+  if (err) { set_error("streamed solver: tick bound or segment check failed"); return PC_ERR_INTERNAL; }
   for (int64_t i = 0; i < nq; ++i) {
     if (!dev_out && q[i].n_percolating) *q[i].n_percolating = (int64_t)cnt[i];
     if (out) {

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/percol.h"
 
@@ -90,7 +91,38 @@ struct Lattice {
   int TWP;       // TW + 2: one zero padding word before and after
   const int32_t* nbr;   // [A][12] neighbour column or A (sentinel) if outside the hexagon
   const int8_t* sigma;  // [A]
+  // Padded-row plane layout of per-layer FP arrays (see lattice.cu):
+  int P;                // entries per plane
+  int s_begin;          // first strip: strip s covers plane positions 3s, 3s+1, 3s+2
+  int n_strips;
+  const int16_t* strip_row;  // [n_strips] hexagon row (0..2W) of each strip
+  const int32_t* row_off;    // [2W+1][4] offsets to rows r-2, r-1, r+1, r+2
+  const int32_t* ppos;       // [A] plane position of each column
+  const int32_t* pcol;       // [P] column at each plane position, -1 for zeros
 };
+
+// Host-side padded-row layout of one W (lattice.cu).
+struct PlaneLayout {
+  int P = 0, s_begin = 0, n_strips = 0;
+  std::vector<int16_t> strip_row;
+  std::vector<int32_t> row_off, ppos, pcol;
+};
+PlaneLayout make_layout(int W);
+int max_segment(int W, int chunk);
+
+// Plane positions [lo, hi) read by the strip at position b whose row has the
+// offsets ro[0..3] (rows r-2, r-1, r+1, r+2): the runs of tiling.cuh.
+__host__ __device__ inline void strip_span(int b, const int32_t* ro, int* lo, int* hi) {
+  const int f0 = b + 1 + ro[0], d0 = b - 1 + ro[1], u0 = b - 2 + ro[2], e0 = b - 1 + ro[3], c0 = b - 1;
+  int l = c0, h = c0 + 5;
+  l = l < f0 ? l : f0; h = h > f0 + 3 ? h : f0 + 3;
+  l = l < d0 ? l : d0; h = h > d0 + 6 ? h : d0 + 6;
+  l = l < u0 ? l : u0; h = h > u0 + 6 ? h : u0 + 6;
+  l = l < e0 ? l : e0; h = h > e0 + 3 ? h : e0 + 3;
+  *lo = l; *hi = h;
+}
+void layout_fill(int W, int* P, int* s_begin, int* n_strips, int16_t* strip_row, int32_t* row_off,
+                 int32_t* ppos, int32_t* pcol);
 
 // error reporting (thread-local message), defined in api.cu
 void set_error(const std::string& msg);

@@ -30,7 +30,7 @@ struct ResidentArgs {
   unsigned long long* work;  // zeroed work counter
   int prep_chunk;            // layers prepared per lazy chunk (>= 3)
 };
-size_t resident_smem(int A, int L);
+size_t resident_smem(const Lattice& lat);
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st);
 pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g,
                             const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out);
@@ -39,7 +39,7 @@ int resident_threads(int A, int L);
 // CTA size picked by the autotuner for (W, L) (tune.cu); times candidates on a
 // miss, outside any stream capture
 int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st);
-bool resident_fits(int A, int L);
+bool resident_fits(int W, int L);
 void release_batches();
 
 // Streamed solver for lattices beyond shared memory, stream.cu.
@@ -63,7 +63,7 @@ pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* d
                           cudaGraphNode_t* last);
 int* stream_plan_error(StreamPlan* P);
 void stream_plan_release(StreamPlan* P, cudaStream_t st);
-size_t stream_slot_bytes(int A, int L);
+size_t stream_slot_bytes(int W, int L);
 pc_status run_stream(const StreamJob& job, cudaStream_t st);
 
 // Server engine (stream.cu): streamed-solver slots bound to queries by the host.

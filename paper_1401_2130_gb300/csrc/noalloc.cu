@@ -35,12 +35,25 @@ namespace pc {
 namespace {
 
 constexpr int kStaticMaxColumns = 8192;       // W <= 51
+constexpr int kStaticMaxW = 51;
+constexpr int kStaticMaxP = 9216;             // plane entries of the widest allowed lattice
+constexpr int kStaticMaxStrips = kStaticMaxP / 3 + 2;
+constexpr int kStaticMaxRows = 2 * kStaticMaxW + 1;
 constexpr int64_t kStaticMaxConfigs = 1 << 18;
 constexpr size_t kCtrBytes = 256;
 constexpr size_t kNbrBytes = sizeof(int32_t) * kStaticMaxColumns * kLateral;
 constexpr size_t kSigBytes = kStaticMaxColumns;
+constexpr size_t kLayBytes = sizeof(int32_t) * (kStaticMaxColumns + kStaticMaxP + 4 * kStaticMaxRows) +
+                             sizeof(int16_t) * kStaticMaxStrips;
 constexpr size_t kOutBytes = (size_t)kStaticMaxConfigs * (1 + 4 + 4 + 4);
-constexpr size_t kStaticBytes = kCtrBytes + kNbrBytes + kSigBytes + kOutBytes;
+constexpr size_t kStaticBytes = kCtrBytes + kNbrBytes + kSigBytes + ((kLayBytes + 255) & ~(size_t)255) + kOutBytes;
+
+// host staging of the layout tables (filled without allocation, then copied)
+std::mutex g_host_mu;
+int32_t h_ppos[kStaticMaxColumns];
+int32_t h_pcol[kStaticMaxP];
+int32_t h_roff[4 * kStaticMaxRows];
+int16_t h_srow[kStaticMaxStrips];
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -121,10 +134,7 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
     set_error("pc_inspect_static: at most 8192 columns (W <= 51)"); return PC_ERR_ARG;
   }
   const int A = (int)A64;
-  int dev = 0, max_smem = 0;
-  PC_CUDA(cudaGetDevice(&dev));
-  PC_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (resident_smem(A, L) > (size_t)max_smem) {
+  if (!resident_fits(W, L)) {
     set_error("pc_inspect_static: lattice state exceeds one CTA's shared memory"); return PC_ERR_ARG;
   }
   if (n_configs > 0 && !verdicts) { set_error("pc_inspect_static: verdicts must not be NULL"); return PC_ERR_ARG; }
@@ -141,7 +151,12 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
   unsigned long long* n_perc = work + 1;
   int32_t* nbr = (int32_t*)(base + kCtrBytes);
   int8_t* sig = (int8_t*)(base + kCtrBytes + kNbrBytes);
-  unsigned char* o = base + kCtrBytes + kNbrBytes + kSigBytes;
+  unsigned char* lay = base + kCtrBytes + kNbrBytes + kSigBytes;
+  int32_t* d_ppos = (int32_t*)lay;
+  int32_t* d_pcol = d_ppos + kStaticMaxColumns;
+  int32_t* d_roff = d_pcol + kStaticMaxP;
+  int16_t* d_srow = (int16_t*)(d_roff + 4 * kStaticMaxRows);
+  unsigned char* o = lay + ((kLayBytes + 255) & ~(size_t)255);
   int32_t* d_fh = (int32_t*)o;
   float* d_mass = (float*)(o + 4 * (size_t)kStaticMaxConfigs);
   int32_t* d_ms = (int32_t*)(o + 8 * (size_t)kStaticMaxConfigs);
@@ -150,20 +165,34 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
   PC_CUDA(cudaMemsetAsync(base, 0, kCtrBytes, st));
   static_tables_kernel<<<(A + 127) / 128, 128, 0, st>>>(W, A, nbr, sig);
   PC_CUDA(cudaGetLastError());
+  int P = 0, s_begin = 0, n_strips = 0;
+  {
+    // pageable copies from static host tables: they synchronise, but allocate nothing
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    layout_fill(W, &P, &s_begin, &n_strips, nullptr, nullptr, nullptr, nullptr);
+    if (P > kStaticMaxP || n_strips > kStaticMaxStrips) {
+      set_error("pc_inspect_static: layout exceeds the static tables"); return PC_ERR_ARG;
+    }
+    layout_fill(W, nullptr, nullptr, nullptr, h_srow, h_roff, h_ppos, h_pcol);
+    PC_CUDA(cudaMemcpyAsync(d_ppos, h_ppos, sizeof(int32_t) * A, cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(d_pcol, h_pcol, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(d_roff, h_roff, sizeof(int32_t) * 4 * (2 * W + 1), cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaMemcpyAsync(d_srow, h_srow, sizeof(int16_t) * n_strips, cudaMemcpyHostToDevice, st));
+    PC_CUDA(cudaStreamSynchronize(st));
+  }
 
   ResidentArgs a;
   a.lat.W = W; a.lat.L = L; a.lat.A = A; a.lat.N = (int64_t)A * L; a.lat.S = A + 1;
   a.lat.TW = (L + 31) / 32; a.lat.TWP = a.lat.TW + 2; a.lat.nbr = nbr; a.lat.sigma = sig;
+  a.lat.P = P; a.lat.s_begin = s_begin; a.lat.n_strips = n_strips;
+  a.lat.strip_row = d_srow; a.lat.row_off = d_roff; a.lat.ppos = d_ppos; a.lat.pcol = d_pcol;
   a.occ.k0 = (uint32_t)(seed & 0xffffffffu); a.occ.k1 = (uint32_t)(seed >> 32);
   a.occ.cfg = 0; a.occ.wl = (uint32_t)W | ((uint32_t)L << 8); a.occ.T = threshold_of(p);
   a.occ_bits = nullptr; a.words_per_cfg = (a.lat.N + 31) / 32;
   a.n_cfg = n_configs; a.cfg0 = (uint32_t)config_begin;
   a.verdict = d_v; a.first_hit = d_fh; a.mass = d_mass; a.m_stop = d_ms;
   a.n_perc = n_perc; a.work = work; a.prep_chunk = 8;
-  const int per = (L + 15) / 16;
-  long long t = ((long long)A * per + 31) / 32 * 32;
-  t = t < 128 ? 128 : (t > 1024 ? 1024 : t);
-  if ((rc = launch_resident(a, (int)t, st))) return rc;
+  if ((rc = launch_resident(a, resident_threads(A, L), st))) return rc;
 
   const size_t n = (size_t)n_configs;
   PC_CUDA(cudaMemcpyAsync(verdicts, d_v, n, cudaMemcpyDeviceToHost, st));

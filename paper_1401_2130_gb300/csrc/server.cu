@@ -165,7 +165,7 @@ pc_status start_query(pc_server* s, uint64_t id, Ticket& t) {
   if ((rc = server_engine_set_query(s->E, t.qi, sq, st))) return rc;
   std::vector<int> slots, qs;
   std::vector<char*> bases;
-  const size_t sb = stream_slot_bytes(lat.A, lat.L);
+  const size_t sb = stream_slot_bytes(lat.W, lat.L);
   for (size_t k = 0; k < t.slot_ids.size(); ++k) {
     slots.push_back(t.slot_ids[k]); qs.push_back(t.qi);
     bases.push_back(s->arena.base + t.off_slots + k * sb);
@@ -228,7 +228,7 @@ void worker_main(pc_server* s) {
         Ticket& t = found->second;
         const pc_query& q = t.q;
         const int64_t A = n_columns(q.W);
-        const bool res = resident_fits((int)A, q.L);
+        const bool res = resident_fits(q.W, q.L);
         size_t off = 0;
         const size_t ob = out_bytes(q.n_configs);
         if (res) {
@@ -241,7 +241,7 @@ void worker_main(pc_server* s) {
           int free_slots = 0;
           for (auto o : s->slot_owner) free_slots += o == 0;
           if (qi < 0 || free_slots == 0) break;
-          const size_t sb = stream_slot_bytes((int)A, q.L);
+          const size_t sb = stream_slot_bytes(q.W, q.L);
           if (!s->arena.alloc(ob, &off)) break;
           const size_t room = s->arena.largest();
           long long k = std::min<long long>(q.n_configs, free_slots);
@@ -398,7 +398,7 @@ pc_status pc_server_submit(pc_server* s, const pc_query* q, uint64_t* ticket) {
   }
   const int64_t A = n_columns(q->W);
   size_t need = out_bytes(q->n_configs);
-  if (!resident_fits((int)A, q->L)) need += stream_slot_bytes((int)A, q->L) + 256;
+  if (!resident_fits(q->W, q->L)) need += stream_slot_bytes(q->W, q->L) + 256;
   if (need > s->opts.hbm_budget_bytes) {
     set_error("pc_server_submit: footprint exceeds the server's HBM budget"); return PC_ERR_OOM;
   }

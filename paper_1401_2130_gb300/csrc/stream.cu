@@ -3,17 +3,21 @@
 // or many queries (W, L, p, seed, configuration range) at once.
 //
 // K "slots" each hold one configuration's state in HBM:
-//   nu[2][(L+2) x S] FP32  nu = mu / deg (ping-pong, rows t+1, zero rows 0 and
-//                          L+1, column A an always-zero sentinel)
-//   dg[L x S]        u8    deg(i) for metallic sites (Eq. (2), detector edge
-//                          included on t = L-1), 0 for insulating ones
+//   nu[2][(L+4) planes] FP32  nu = mu / deg (ping-pong), layer t in plane t+2
+//                          of the padded-row layout (lattice.cu); planes 0, 1,
+//                          L+2, L+3 and all padding zero
+//   dg[L planes]     u8    deg(i) for metallic sites (Eq. (2), detector edge
+//                          included on t = L-1), 0 elsewhere
 //   occw, R[2]       bits  occupancy and reached set, words [tw+1][a] of 32
 //                          consecutive tube indices of column a
 // A slot takes configurations from a global work list (all queries, largest
 // lattices first) and is refilled as soon as its configuration finishes.
 // The device runs "ticks" inside one CUDA graph conditional WHILE node:
 //   sweep   : all CTAs walk a global list of work units over all slots --
-//             FP32 site updates of step m over the causal window t <= m, the
+//             FP32 site updates of step m over the causal window t <= m (a
+//             chunk of strips walks up a chunk of layers; the plane segment
+//             the chunk reads is staged into shared memory by TMA bulk copies
+//             through a 4-deep ring, three layers ahead of the compute), the
 //             exact bit-parallel reached-set update, and lazy preparation of
 //             the layers just ahead of the window (Philox draw of a word row,
 //             degrees, zeroing of nu and R rows);
@@ -30,6 +34,8 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tiling.cuh"
+#include "tma.cuh"
 
 namespace pc {
 
@@ -39,7 +45,9 @@ constexpr uint32_t kGrow = 1u, kEnd = 2u;
 enum : int { PH_EMPTY = 0, PH_DRAW0 = 1, PH_PREP0 = 2, PH_STEP = 3 };
 enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS = 5 };
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
-constexpr int kRows = 16;     // layers (or word rows) per FP / BITS / PREP unit
+constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
+constexpr int kRowsFP = 64;   // layers per FP unit (the ring prologue is paid once per unit)
+constexpr int kRing = 8;      // ring slots: planes in flight ahead of the compute
 constexpr int kMaxSlots = 1024;
 
 struct QDev {
@@ -80,6 +88,7 @@ struct Ctx {
   int* error;
   unsigned int max_ticks;
   cudaGraphConditionalHandle cond;
+  int seg_cap;                  // floats per shared-memory ring slot of the FP units
   int use_cond;                 // set the WHILE condition at the end of a tick
   int server;                   // 1: slots are bound to a query by the host
   char** slot_base;             // [K] state of each slot (server mode)
@@ -124,10 +133,16 @@ __host__ __device__ inline Plan make_plan(int phase, int m, int G, int F, int L,
   return p;
 }
 
-__host__ __device__ inline int units_of(int kind, int lo, int hi, int A) {
+// items along the plane / column axis of one unit row, per kind: strips for
+// FP, plane positions for PREP and CLEAN, columns for BITS and DRAW
+__host__ __device__ inline int width_of(int kind, const Lattice& lat) {
+  return kind == U_FP ? lat.n_strips : (kind == U_PREP || kind == U_CLEAN) ? lat.P : lat.A;
+}
+
+__host__ __device__ inline int units_of(int kind, int lo, int hi, const Lattice& lat) {
   if (hi <= lo) return 0;
-  const int ccol = (A + kCols - 1) / kCols;
-  const int per = (kind == U_DRAW || kind == U_CLEAN) ? 1 : kRows;
+  const int ccol = (width_of(kind, lat) + kCols - 1) / kCols;
+  const int per = (kind == U_DRAW || kind == U_CLEAN) ? 1 : kind == U_FP ? kRowsFP : kRows;
   return ccol * ((hi - lo + per - 1) / per);
 }
 
@@ -138,9 +153,9 @@ struct SlotView {
 
 __host__ __device__ inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-__host__ __device__ inline size_t slot_bytes_of(int A, int L) {
+__host__ __device__ inline size_t slot_bytes_of(int A, int L, int P) {
   const size_t S = (size_t)A + 1, TWP = (size_t)(L + 31) / 32 + 2;
-  return 2 * a256(sizeof(float) * (size_t)(L + 2) * S) + a256((size_t)L * S) +
+  return 2 * a256(sizeof(float) * (size_t)(L + 4) * P) + a256((size_t)L * P) +
          3 * a256(sizeof(uint32_t) * TWP * S);
 }
 
@@ -148,11 +163,11 @@ __device__ inline SlotView view_of(const Ctx& x, int slot, const Lattice& lat) {
   const size_t S = (size_t)lat.S;
   char* b = x.server ? x.slot_base[slot] : x.pool + (size_t)slot * x.slot_bytes;
   SlotView v;
-  const size_t nu_b = a256(sizeof(float) * (size_t)(lat.L + 2) * S);
+  const size_t nu_b = a256(sizeof(float) * (size_t)(lat.L + 4) * lat.P);
   const size_t w_b = a256(sizeof(uint32_t) * (size_t)lat.TWP * S);
   v.nu0 = (float*)b; b += nu_b;
   v.nu1 = (float*)b; b += nu_b;
-  v.dg = (uint8_t*)b; b += a256((size_t)lat.L * S);
+  v.dg = (uint8_t*)b; b += a256((size_t)lat.L * lat.P);
   v.occw = (uint32_t*)b; b += w_b;
   v.R0 = (uint32_t*)b; b += w_b;
   v.R1 = (uint32_t*)b;
@@ -179,7 +194,7 @@ __device__ inline int query_of(const Ctx& x, long long item) {
 
 __device__ inline void fill_plan(Ctl& c, const Lattice& lat) {
   const Plan p = make_plan(c.phase, c.m, c.G, c.F, lat.L, lat.TW);
-  for (int k = 0; k < U_KINDS; ++k) c.units[k] = units_of(k, p.lo[k], p.hi[k], lat.A);
+  for (int k = 0; k < U_KINDS; ++k) c.units[k] = units_of(k, p.lo[k], p.hi[k], lat);
 }
 
 __device__ inline void assign(const Ctx& x, Ctl& c, unsigned long long item) {
@@ -266,12 +281,130 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
   plan_prefix(x);
 }
 
-__global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
+
+// One FP unit: strips [k0, k0 + kCols) (one per thread) over layers
+// [t0, t1).  Layer t reads planes t+1, t+2, t+3; the segment [lo, hi) of each
+// plane the chunk touches is copied into ring slot (plane mod kRing) by one
+// thread (cp.async.bulk, mbarrier completion), kRing - 1 planes ahead of its
+// use.  ph holds the expected parity of each slot's barrier (identical in all
+// threads).
+__device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat, const SlotView& v, bool odd,
+                                               int k0, int t0, int t1, float* ring, uint64_t* bars,
+                                               uint32_t& ph, const float* inv, int* s_red) {
+  const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap;
+  const int k = k0 + tid;
+  const bool have = k < lat.n_strips;
+  int b = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+  int lo = 0x7fffffff, hi = -0x7fffffff;
+  if (have) {
+    b = 3 * (lat.s_begin + k);
+    const int32_t* ro = lat.row_off + 4 * lat.strip_row[k];
+    r0 = __ldg(ro); r1 = __ldg(ro + 1); r2 = __ldg(ro + 2); r3 = __ldg(ro + 3);
+    const int32_t rr[4] = {r0, r1, r2, r3};
+    strip_span(b, rr, &lo, &hi);
+  }
+  // segment of the chunk: block min / max
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (tid == 0) { s_red[0] = 0x7fffffff; s_red[1] = -0x7fffffff; }
+  __syncthreads();
+  if ((tid & 31) == 0) { atomicMin(&s_red[0], lo); atomicMax(&s_red[1], hi); }
+  __syncthreads();
+  const int lo_al = s_red[0] & ~3;
+  int seg = ((s_red[1] + 3) & ~3) - lo_al;
+  if (seg > cap) {  // cannot happen: the host sized the ring for every lattice
+    if (tid == 0) atomicOr(x.error, 4);
+    seg = cap;
+  }
+  const float* src = odd ? v.nu0 : v.nu1;
+  float* dst = odd ? v.nu1 : v.nu0;
+  const int last = t1 + 2;
+  auto issue = [&](int pl) {
+    if (tid == 0 && pl <= last) {
+      const int sl = pl % kRing;
+      fence_proxy_async_shared();
+      mbar_arrive_expect_tx(&bars[sl], (unsigned)seg * 4u);
+      bulk_g2s(ring + (size_t)sl * cap, src + (size_t)pl * P + lo_al, (unsigned)seg * 4u, &bars[sl]);
+    }
+  };
+  auto wait = [&](int pl) {
+    const int sl = pl % kRing;
+    if (!mbar_wait(&bars[sl], (ph >> sl) & 1u) && tid == 0) atomicOr(x.error, 2);
+    ph ^= 1u << sl;
+  };
+  auto slot = [&](int pl) { return ring + (size_t)(pl % kRing) * cap; };
+  const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
+  const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al;
+
+  for (int i = 1; i <= kRing; ++i) issue(t0 + i);
+  wait(t0 + 1);
+  wait(t0 + 2);
+  float up2 = 0.f, dp2 = 0.f, cp[4] = {0.f, 0.f, 0.f, 0.f};
+  Runs A, B;
+  if (have) {
+    const float* pl = slot(t0 + 1);
+    up2 = pl[u0 + 2]; dp2 = pl[d0 + 2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cp[i] = pl[c0 + i];
+    load_runs(A, slot(t0 + 2), u0, d0, c0);
+  }
+  __syncthreads();  // plane t0+1's slot is free
+  issue(t0 + kRing + 1);
+  // degrees are read from HBM one layer ahead of their use
+  const uint8_t* dgb = v.dg + b;
+  int g0 = 0, g1 = 0, g2 = 0;
+  if (have) { const uint8_t* d = dgb + (size_t)t0 * P; g0 = d[0]; g1 = d[1]; g2 = d[2]; }
+  int t = t0;
+  for (;;) {
+    int h0 = 0, h1 = 0, h2 = 0;
+    if (have && t + 1 < t1) { const uint8_t* d = dgb + (size_t)(t + 1) * P; h0 = d[0]; h1 = d[1]; h2 = d[2]; }
+    wait(t + 3);
+    if (have) {
+      load_runs(B, slot(t + 3), u0, d0, c0);
+      strip_emit_deg(A, B, up2, dp2, cp, slot(t + 2), e0, f0, dst + (size_t)(t + 2) * P, b,
+                     g0, g1, g2, inv);
+      up2 = A.U[2]; dp2 = A.D[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
+    }
+    g0 = h0; g1 = h1; g2 = h2;
+    __syncthreads();  // plane t+2's slot is free
+    issue(t + kRing + 2);
+    if (++t >= t1) break;
+    if (have && t + 1 < t1) { const uint8_t* d = dgb + (size_t)(t + 1) * P; h0 = d[0]; h1 = d[1]; h2 = d[2]; }
+    wait(t + 3);
+    if (have) {
+      load_runs(A, slot(t + 3), u0, d0, c0);
+      strip_emit_deg(B, A, up2, dp2, cp, slot(t + 2), e0, f0, dst + (size_t)(t + 2) * P, b,
+                     g0, g1, g2, inv);
+      up2 = B.U[2]; dp2 = B.D[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
+    }
+    g0 = h0; g1 = h1; g2 = h2;
+    __syncthreads();
+    issue(t + kRing + 2);
+    if (++t >= t1) break;
+  }
+}
+
+__global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
+  extern __shared__ __align__(128) float ring[];  // kRing slots of x.seg_cap floats
   __shared__ float inv_deg[16];
   __shared__ uint32_t s_flag;
+  __shared__ int s_red[2];
+  __shared__ __align__(8) uint64_t bars[kRing];
   const int tid = threadIdx.x;
   if (tid < 16) inv_deg[tid] = tid ? __frcp_rn((float)tid) : 0.f;
+  if (tid == 0) {
+    for (int i = 0; i < kRing; ++i) mbar_init(&bars[i], 1);
+    mbar_fence_init();
+  }
   __syncthreads();
+  uint32_t ph = 0;  // expected parity per ring slot
   const int total = x.pre[x.K];
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     // slot: last s with pre[s] <= u (binary search)
@@ -286,35 +419,17 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
     while (local >= c.units[kind]) { local -= c.units[kind]; ++kind; }
     const QDev& Q = x.qs[c.q];
     const Lattice& lat = Q.lat;
-    const int A = lat.A, L = lat.L, S = lat.S;
-    const int ccol = (A + kCols - 1) / kCols;
+    const int A = lat.A, L = lat.L, S = lat.S, P = lat.P;
+    const int ccol = (width_of(kind, lat) + kCols - 1) / kCols;
     const int cchunk = local % ccol, rchunk = local / ccol;
-    const int a = cchunk * kCols + tid;
+    const int a = cchunk * kCols + tid;  // column, strip or plane position
     const Plan p = make_plan(c.phase, c.m, c.G, c.F, L, lat.TW);
     const SlotView v = view_of(x, slot, lat);
 
     if (kind == U_FP) {
-      const int t0 = p.lo[U_FP] + rchunk * kRows;
-      const int t1 = min(t0 + kRows, p.hi[U_FP]);
-      const bool odd = (c.m & 1) != 0;  // step m reads buffer (m-1)&1, writes m&1
-      const float* __restrict__ src = odd ? v.nu0 : v.nu1;
-      float* __restrict__ dst = odd ? v.nu1 : v.nu0;
-      if (a < A) {
-        const int sg = lat.sigma[a];
-        int off[kLateral];
-#pragma unroll
-        for (int d = 0; d < kLateral; ++d) off[d] = dir_dt(d, sg) * S + lat.nbr[a * kLateral + d];
-        float below = src[t0 * S + a], here = src[(t0 + 1) * S + a];
-        for (int t = t0; t < t1; ++t) {
-          const int base = (t + 1) * S;
-          const float above = src[base + S + a];
-          float s = below + above;
-#pragma unroll
-          for (int d = 0; d < kLateral; ++d) s += src[base + off[d]];
-          dst[base + a] = inv_deg[v.dg[t * S + a]] * s;
-          below = here; here = above;
-        }
-      }
+      const int t0 = p.lo[U_FP] + rchunk * kRowsFP;
+      const int t1 = min(t0 + kRowsFP, p.hi[U_FP]);
+      fp_unit_staged(x, lat, v, (c.m & 1) != 0, cchunk * kCols, t0, t1, ring, bars, ph, inv_deg, s_red);
     } else if (kind == U_BITS) {
       const int w0 = p.lo[U_BITS] + rchunk * kRows;
       const int w1 = min(w0 + kRows, p.hi[U_BITS]);
@@ -349,43 +464,49 @@ __global__ void __launch_bounds__(kCols) sweep_kernel(Ctx x) {
     } else if (kind == U_PREP) {
       const int t0 = p.lo[U_PREP] + rchunk * kRows;
       const int t1 = min(t0 + kRows, p.hi[U_PREP]);
-      if (a < A) {
-        const int sg = lat.sigma[a];
+      const int pos = a;
+      if (pos < P) {
+        const int col = __ldg(lat.pcol + pos);
         int nb[kLateral];
+        int sg = 0;
+        if (col >= 0) {
+          sg = lat.sigma[col];
 #pragma unroll
-        for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
+          for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[col * kLateral + d];
+        }
         for (int t = t0; t < t1; ++t) {
           int deg = 0;
-          if (bit_at(v.occw, S, a, t)) {
-            deg = (int)bit_at(v.occw, S, a, t - 1) + (int)bit_at(v.occw, S, a, t + 1) + (t == L - 1);
+          if (col >= 0 && bit_at(v.occw, S, col, t)) {
+            deg = (int)bit_at(v.occw, S, col, t - 1) + (int)bit_at(v.occw, S, col, t + 1) + (t == L - 1);
 #pragma unroll
             for (int d = 0; d < kLateral; ++d) deg += (int)bit_at(v.occw, S, nb[d], t + dir_dt(d, sg));
           }
-          v.dg[t * S + a] = (uint8_t)deg;
-          v.nu0[(t + 1) * S + a] = 0.f;
-          v.nu1[(t + 1) * S + a] = 0.f;
-          if ((t & 31) == 0) {  // reached-set word rows cleaned one row ahead
+          v.dg[(size_t)t * P + pos] = (uint8_t)deg;
+          v.nu0[(size_t)(t + 2) * P + pos] = 0.f;
+          v.nu1[(size_t)(t + 2) * P + pos] = 0.f;
+          if (col >= 0 && (t & 31) == 0) {  // reached-set word rows cleaned one row ahead
             const int wr = (t >> 5) + 2;
-            v.R0[wr * S + a] = 0u; v.R1[wr * S + a] = 0u;
-            if (t == 0) { v.R0[S + a] = 0u; v.R1[S + a] = 0u; }
+            v.R0[wr * S + col] = 0u; v.R1[wr * S + col] = 0u;
+            if (t == 0) { v.R0[S + col] = 0u; v.R1[S + col] = 0u; }
           }
         }
       }
     } else if (kind == U_CLEAN) {
-      // padding rows 0 and L+1 of nu, 0 and TW+1 of the bit arrays
+      // zero planes 0, 1, L+2, L+3 of nu, pad rows 0 and TW+1 of the bit arrays
+      if (a < P) {
+        const size_t hi0 = (size_t)(L + 2) * P;
+        v.nu0[a] = 0.f; v.nu0[P + a] = 0.f; v.nu0[hi0 + a] = 0.f; v.nu0[hi0 + P + a] = 0.f;
+        v.nu1[a] = 0.f; v.nu1[P + a] = 0.f; v.nu1[hi0 + a] = 0.f; v.nu1[hi0 + P + a] = 0.f;
+      }
       if (a <= A) {
-        v.nu0[a] = 0.f; v.nu1[a] = 0.f;
-        v.nu0[(L + 1) * S + a] = 0.f; v.nu1[(L + 1) * S + a] = 0.f;
         const int top = (lat.TW + 1) * S + a;
         v.occw[a] = 0u; v.R0[a] = 0u; v.R1[a] = 0u;
         v.occw[top] = 0u; v.R0[top] = 0u; v.R1[top] = 0u;
       }
-      if (cchunk == 0) {  // the sentinel column A of every row
-        for (int r = tid; r < L + 2; r += kCols) { v.nu0[r * S + A] = 0.f; v.nu1[r * S + A] = 0.f; }
+      if (cchunk == 0)  // the sentinel column A of every word row
         for (int r = tid; r < lat.TWP; r += kCols) {
           v.occw[r * S + A] = 0u; v.R0[r * S + A] = 0u; v.R1[r * S + A] = 0u;
         }
-      }
     } else {  // U_DRAW: one word row of occupancy, 32 tubes per word
       const int tw = p.lo[U_DRAW] + rchunk;
       if (a < A) {
@@ -473,9 +594,10 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
         for (int a = tid; a < A; a += blockDim.x) {
           const uint32_t b = v.occw[S + a] & 1u;
           v.R0[S + a] = b;
-          const int d = v.dg[a];
+          const int pos = __ldg(lat.ppos + a);
+          const int d = v.dg[pos];
           const float val = b ? (d ? __frcp_rn((float)d) : 0.f) * inv : 0.f;
-          v.nu0[S + a] = val;
+          v.nu0[(size_t)2 * lat.P + pos] = val;
           part += val;
         }
         if (L == 1) {
@@ -492,7 +614,7 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
       if (f & kEnd) {
         const float* dst = (c.m & 1) ? v.nu1 : v.nu0;
         float part = 0.f;
-        for (int a = tid; a < A; a += blockDim.x) part += dst[L * S + a];
+        for (int k = tid; k < lat.P; k += blockDim.x) part += dst[(size_t)(L + 1) * lat.P + k];
         mass = block_sum_f(part, red);
         finish = true; verdict = 1; fh = c.m + 1; mstop = c.m + 1;
       } else if (!(f & kGrow)) {
@@ -550,7 +672,11 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
 
 }  // namespace
 
-size_t stream_slot_bytes(int A, int L) { return slot_bytes_of(A, L); }
+size_t stream_slot_bytes(int W, int L) {
+  int P = 0;
+  layout_fill(W, &P, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return slot_bytes_of((int)n_columns(W), L, P);
+}
 
 struct StreamPlan {
   Ctx x;
@@ -570,7 +696,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
     h[i].words_per_cfg = qs[i].words_per_cfg; h[i].n_cfg = qs[i].n_cfg; h[i].cfg0 = qs[i].cfg0;
     h[i].out = qs[i].out; h[i].item0 = n_items;
     n_items += qs[i].n_cfg;
-    slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L));
+    slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L, qs[i].lat.P));
     max_steps = std::max<unsigned long long>(max_steps, (unsigned long long)qs[i].lat.N + 4);
   }
   size_t free_b = 0, total_b = 0;
@@ -607,6 +733,14 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   x.pool = q;
   x.slot_bytes = slot;
   x.use_cond = 0; x.server = 0; x.slot_base = nullptr; x.qnext = nullptr; x.qdone = nullptr;
+  {
+    int cap = 4;
+    for (int i = 0; i < nq; ++i) cap = std::max(cap, max_segment(qs[i].lat.W, kCols) + 8);
+    x.seg_cap = cap;
+    const int bytes = kRing * cap * (int)sizeof(float);
+    cudaError_t ea = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (ea != cudaSuccess) { cudaFreeAsync(P->mem, st); delete P; return cuda_fail(ea, "sweep smem"); }
+  }
   // every configuration needs at most N + 3 ticks; slots run concurrently
   const unsigned long long waves = (unsigned long long)((n_items + K - 1) / K);
   const unsigned long long bound = waves * (max_steps + 4) + 64;
@@ -654,6 +788,7 @@ pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* d
   cudaKernelNodeParams sp = {};
   sp.func = (void*)sweep_kernel;
   sp.gridDim = dim3(P->grid); sp.blockDim = dim3(kCols); sp.kernelParams = args;
+  sp.sharedMemBytes = (unsigned)(kRing * x.seg_cap * sizeof(float));
   cudaGraphNode_t n_sweep, n_ctl;
   PC_CUDA(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &sp));
   cudaKernelNodeParams cpk = {};
@@ -761,6 +896,7 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
   x.error = (int*)(x.ticks + 2);
   x.pool = nullptr; x.slot_bytes = 0; x.max_ticks = 0xffffffffu;
   x.use_cond = 0; x.server = 1;
+  x.seg_cap = max_segment(255, kCols) + 8;  // any lattice the server accepts
   E->max_queries = nq;
   pc_status rc = PC_OK;
   do {
@@ -772,6 +908,10 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kRing * x.seg_cap * (int)sizeof(float))) != cudaSuccess) {
+      rc = cuda_fail(e, "sweep smem"); break;
+    }
     cudaGraph_t g;
     if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) { rc = cuda_fail(e, "graph"); break; }
     void* args[] = {&x};
@@ -780,6 +920,7 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
       cudaKernelNodeParams sp = {};
       sp.func = (void*)sweep_kernel; sp.gridDim = dim3(nsm * 8); sp.blockDim = dim3(kCols);
       sp.kernelParams = args;
+      sp.sharedMemBytes = (unsigned)(kRing * x.seg_cap * sizeof(float));
       cudaGraphNode_t ns, nc;
       if ((e = cudaGraphAddKernelNode(&ns, g, prev ? &prev : nullptr, prev ? 1 : 0, &sp)) != cudaSuccess) { rc = cuda_fail(e, "node"); break; }
       cudaKernelNodeParams cp = {};
@@ -863,6 +1004,25 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st) {
   StreamPlan* P = nullptr;
   pc_status rc = stream_plan_create(&q, 1, st, &P);
   if (rc) return rc;
+  if (std::getenv("PC_STREAM_HOST_LOOP")) {
+    // profiling aid: the same ticks launched from a host loop (profilers do
+    // not look inside graphs with conditional nodes)
+    Ctx& x = P->x;
+    stream_init_kernel<<<1, 1024, 0, st>>>(x);
+    unsigned long long done = 0;
+    for (int chunk = 0; rc == PC_OK && done < (unsigned long long)x.n_items; ++chunk) {
+      for (int i = 0; i < 32; ++i) {
+        sweep_kernel<<<P->grid, kCols, kRing * x.seg_cap * sizeof(float), st>>>(x);
+        control_kernel<<<x.K, kCols, 0, st>>>(x);
+      }
+      cudaError_t e = cudaMemcpyAsync(&done, x.n_done, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "host loop");
+      if ((unsigned long long)chunk * 32 > x.max_ticks) { set_error("streamed solver did not converge"); rc = PC_ERR_INTERNAL; }
+    }
+    stream_plan_release(P, st);
+    return rc;
+  }
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   do {
