@@ -320,8 +320,8 @@ def run_serving(args, pc, torch):
         plain.append(pc.pc_inspect(*sp))
         svc.append(time.perf_counter() - t0)
     t_plain = float(sum(svc))
-    opts = dict(hbm_budget_bytes=args.serve_budget_gb << 30, max_slots=512, max_slots_per_query=128,
-                ticks_per_poll=8)
+    opts = dict(hbm_budget_bytes=args.serve_budget_gb << 30, max_slots=4096, max_slots_per_query=1024,
+                ticks_per_poll=8, max_W=64)
 
     def serve(arrivals):
         srv = pc.Server(**opts)
@@ -383,14 +383,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ref-per-p", type=int, default=200)
-    ap.add_argument("--cpu-per-p", type=int, default=2000)
+    ap.add_argument("--ref-per-p", type=int, default=1000)
+    ap.add_argument("--cpu-per-p", type=int, default=N_CFG)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--configs-per-p", type=int, default=N_CFG,
                     help="smaller cases for profiling only; the benchmark workload is 10^4")
     ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch", "serving"])
     ap.add_argument("--serve-queries", type=int, default=24)
-    ap.add_argument("--serve-budget-gb", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--large-configs", type=int, default=64)
     ap.add_argument("--batch-configs", type=int, default=10_000)
     args = ap.parse_args()

@@ -180,10 +180,13 @@ typedef struct pc_server pc_server;
 
 typedef struct pc_server_opts {
   uint64_t hbm_budget_bytes;   /* device arena (default 8 GiB) */
-  int32_t max_slots;           /* streamed-solver slots, 1..1024 (default 256) */
+  int32_t max_slots;           /* streamed-solver slots, 1..4096 (default 256) */
   int32_t max_slots_per_query; /* cap per query (default 64) */
   int32_t ticks_per_poll;      /* device ticks between admissions (default 8) */
   int64_t max_pending;         /* queue bound; submit returns PC_ERR_BUSY beyond */
+  int32_t max_W;               /* widest lattice solved in HBM slots, 0..255 (0 = 255):
+                                  sizes the sweep's shared-memory staging; a
+                                  narrower bound lets more planes be in flight */
 } pc_server_opts;
 
 typedef struct pc_server_stats {
@@ -198,7 +201,8 @@ pc_status pc_server_create(const pc_server_opts* opts, pc_server** out);
 /*
  * Enqueue a query (n_configs >= 1).  Its output pointers are HOST pointers
  * (optional), filled when the query completes.  Returns a ticket at once.
- * Errors: PC_ERR_ARG, PC_ERR_OOM (footprint larger than the whole budget),
+ * Errors: PC_ERR_ARG (also: a lattice that needs HBM slots and is wider
+ * than the server's max_W), PC_ERR_OOM (footprint larger than the whole budget),
  * PC_ERR_BUSY (queue full), PC_ERR_CANCELLED (server shutting down).
  */
 pc_status pc_server_submit(pc_server* s, const pc_query* q, uint64_t* ticket);

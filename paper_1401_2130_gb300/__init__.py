@@ -291,7 +291,7 @@ class PcServerOpts(ctypes.Structure):
     """Mirror of pc_server_opts."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("max_slots_per_query", ctypes.c_int32), ("ticks_per_poll", ctypes.c_int32),
-                ("max_pending", ctypes.c_int64)]
+                ("max_pending", ctypes.c_int64), ("max_W", ctypes.c_int32)]
 
 
 class PcServerStats(ctypes.Structure):
@@ -304,10 +304,10 @@ class PcServerStats(ctypes.Structure):
 
 def pc_server_create(hbm_budget_bytes: int = 8 << 30, max_slots: int = 256,
                      max_slots_per_query: int = 64, ticks_per_poll: int = 8,
-                     max_pending: int = 1 << 16) -> int:
+                     max_pending: int = 1 << 16, max_W: int = 0) -> int:
     """Create a serving loop on the current CUDA device; returns its handle."""
     opts = PcServerOpts(hbm_budget_bytes, max_slots, max_slots_per_query, ticks_per_poll,
-                        max_pending)
+                        max_pending, max_W)
     h = ctypes.c_void_p()
     _check(load().pc_server_create(ctypes.addressof(opts), ctypes.addressof(h)))
     return h.value

@@ -11,6 +11,7 @@
 // The instantiated graph and its device memory are cached per batch (same
 // queries, output pointers and flags) and replayed by later calls.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -18,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -26,14 +28,21 @@
 namespace pc {
 
 // ---------------------------------------------------------------------------
-// Autotuner: per (W, L), the resident CTA size with the lowest measured time
-// on a sample of configurations; kept in memory and in PC_TUNE_FILE.
+// Autotuner: per (W, L, p bin), the resident CTA size with the lowest
+// measured time on a sample of configurations; kept in memory and in
+// PC_TUNE_FILE.  p matters: below the threshold configurations stop after a
+// few short steps, above it they sweep the whole fibre, and the best CTA
+// size differs between the two regimes.
 // ---------------------------------------------------------------------------
 namespace {
 
+constexpr double kTunePBins = 40.0;  // p bins of width 0.025
+
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tune;
+std::map<std::tuple<int, int, int>, int> g_tune;
 bool g_tune_loaded = false;
+
+int p_bin(double p) { return (int)std::lround(p * kTunePBins); }
 
 void tune_load() {
   if (g_tune_loaded) return;
@@ -42,12 +51,12 @@ void tune_load() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  // format: {"W,L": T, ...}
-  int W, L, T;
+  // format: {"W,L,pbin": T, ...}
+  int W, L, B, T;
   int ch;
   while ((ch = std::fgetc(f)) != EOF) {
     if (ch != '"') continue;
-    if (std::fscanf(f, "%d,%d\": %d", &W, &L, &T) == 3 && T > 0) g_tune[{W, L}] = T;
+    if (std::fscanf(f, "%d,%d,%d\": %d", &W, &L, &B, &T) == 4 && T > 0) g_tune[{W, L, B}] = T;
   }
   std::fclose(f);
 }
@@ -61,7 +70,8 @@ void tune_save() {
   std::fputs("{", f);
   bool first = true;
   for (auto& kv : g_tune) {
-    std::fprintf(f, "%s\"%d,%d\": %d", first ? "" : ", ", kv.first.first, kv.first.second, kv.second);
+    std::fprintf(f, "%s\"%d,%d,%d\": %d", first ? "" : ", ", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), kv.second);
     first = false;
   }
   std::fputs("}\n", f);
@@ -74,7 +84,8 @@ void tune_save() {
 int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_load();
-  auto it = g_tune.find({lat.W, lat.L});
+  const std::tuple<int, int, int> key{lat.W, lat.L, p_bin(p)};
+  auto it = g_tune.find(key);
   if (it != g_tune.end()) return it->second;
   const int fallback = resident_threads(lat.A, lat.L);
   const int64_t n = 2048;
@@ -114,7 +125,7 @@ int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st) 
   cudaEventDestroy(e1);
   cudaFreeAsync(mem, st);
   cudaStreamSynchronize(st);
-  g_tune[{lat.W, lat.L}] = best;
+  g_tune[key] = best;
   tune_save();
   return best;
 }

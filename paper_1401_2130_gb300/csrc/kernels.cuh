@@ -68,7 +68,7 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st);
 
 // Server engine (stream.cu): streamed-solver slots bound to queries by the host.
 struct ServerEngine;
-pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk,
+pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk, int max_W,
                                cudaStream_t st, ServerEngine** out);
 void server_engine_destroy(ServerEngine* E);
 int server_engine_slots(const ServerEngine* E);

@@ -26,7 +26,8 @@ int64_t n_columns(int W) { return 3ll * W * (W + 1) + 1; }
 // plane and stands for the rows W+1, W+2.  Every neighbour of a column in
 // rows r-2..r+2 then sits at a fixed offset from the column's own position
 // -- position(q, r') = base(r') + q -- and inside the same plane.  P is a
-// multiple of 4 (16-byte plane alignment for bulk copies).  Strips are
+// multiple of 16, so that every plane of the FP32 array and of the byte
+// degree array starts on a 16-byte boundary (bulk copies).  Strips are
 // triples of positions 3s, 3s+1, 3s+2 (sublattice 0, 1, 2); zero positions
 // have degree 0, so a strip may cover zeros and simply writes zeros there.
 // Fills the layout of radius W into caller buffers (any may be null) and
@@ -48,7 +49,7 @@ void layout_fill(int W, int* P_out, int* s_begin_out, int* n_strips_out, int16_t
     pos = x + len(ri);
   }
   const int zone = pos;                      // bottom zone [zone, zone + Z)
-  const int P = (zone + Z + 3) & ~3;
+  const int P = (zone + Z + 15) & ~15;
   // base(row) = position(q, row) - q, for rows -W-2 .. W+2 (index ri + 2)
   auto base = [&](int ri_ext) -> int {
     if (ri_ext <= 1) return 3;                  // rows -W-2, -W-1: q in [-3, W+4]
@@ -83,7 +84,7 @@ void layout_fill(int W, int* P_out, int* s_begin_out, int* n_strips_out, int16_t
 }
 
 // Plane positions [lo, hi) that the strips [k0, k1) read in one plane, for
-// every chunk of `chunk` strips; returns the largest hi - lo (aligned to 4).
+// every chunk of `chunk` strips; returns the largest hi - lo (aligned to 16).
 int max_segment(int W, int chunk) {
   const PlaneLayout L = make_layout(W);
   int best = 0;
@@ -95,8 +96,8 @@ int max_segment(int W, int chunk) {
       strip_span(3 * (L.s_begin + k), &L.row_off[4 * L.strip_row[k]], &sl, &sh);
       lo = std::min(lo, sl); hi = std::max(hi, sh);
     }
-    lo &= ~3;
-    hi = (hi + 3) & ~3;
+    lo &= ~15;
+    hi = (hi + 15) & ~15;
     best = std::max(best, hi - lo);
   }
   return best;

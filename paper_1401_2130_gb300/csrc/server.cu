@@ -350,9 +350,11 @@ pc_status pc_server_create(const pc_server_opts* opts, pc_server** out) {
   o.max_slots_per_query = 64;
   o.ticks_per_poll = 8;
   o.max_pending = 1 << 16;
+  o.max_W = 255;
   if (opts) o = *opts;
-  if (o.hbm_budget_bytes < (1u << 20) || o.max_slots < 1 || o.max_slots > 1024 || o.ticks_per_poll < 1 ||
-      o.max_pending < 1 || o.max_slots_per_query < 1) {
+  if (o.max_W == 0) o.max_W = 255;
+  if (o.hbm_budget_bytes < (1u << 20) || o.max_slots < 1 || o.max_slots > 4096 || o.ticks_per_poll < 1 ||
+      o.max_pending < 1 || o.max_slots_per_query < 1 || o.max_W < 0 || o.max_W > 255) {
     set_error("pc_server_create: bad options"); return PC_ERR_ARG;
   }
   pc_server* s = new pc_server();
@@ -371,7 +373,7 @@ pc_status pc_server_create(const pc_server_opts* opts, pc_server** out) {
   }
   s->arena.init(s->arena_mem, o.hbm_budget_bytes);
   const int max_queries = std::min(o.max_slots, 256);
-  pc_status rc = server_engine_create(o.max_slots, max_queries, o.ticks_per_poll, s->tick, &s->E);
+  pc_status rc = server_engine_create(o.max_slots, max_queries, o.ticks_per_poll, o.max_W, s->tick, &s->E);
   if (rc) {
     cudaFree(s->arena_mem);
     cudaStreamDestroy(s->tick);
@@ -396,9 +398,11 @@ pc_status pc_server_submit(pc_server* s, const pc_query* q, uint64_t* ticket) {
       q->config_begin + q->n_configs > ((int64_t)1 << 32)) {
     set_error("pc_server_submit: bad p or configuration range"); return PC_ERR_ARG;
   }
-  const int64_t A = n_columns(q->W);
   size_t need = out_bytes(q->n_configs);
-  if (!resident_fits(q->W, q->L)) need += stream_slot_bytes(q->W, q->L) + 256;
+  if (!resident_fits(q->W, q->L)) {
+    if (q->W > s->opts.max_W) { set_error("pc_server_submit: lattice wider than the server's max_W"); return PC_ERR_ARG; }
+    need += stream_slot_bytes(q->W, q->L) + 256;
+  }
   if (need > s->opts.hbm_budget_bytes) {
     set_error("pc_server_submit: footprint exceeds the server's HBM budget"); return PC_ERR_OOM;
   }

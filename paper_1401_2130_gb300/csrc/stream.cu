@@ -47,8 +47,21 @@ enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS 
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
 constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
 constexpr int kRowsFP = 64;   // layers per FP unit (the ring prologue is paid once per unit)
-constexpr int kRing = 8;      // ring slots: planes in flight ahead of the compute
-constexpr int kMaxSlots = 1024;
+constexpr int kMaxRing = 16;  // ring slots: planes in flight ahead of the compute
+// shared memory the ring may take per CTA (two sweep CTAs per SM)
+constexpr int kRingBudget = 104 * 1024;
+constexpr int kMaxSlots = 4096;
+
+// ring depth for slots of cap entries (4 B of nu + 1 B of degree each): as
+// deep as the budget allows, at least 3 (a layer reads two planes and needs
+// one in flight)
+inline int ring_depth(int cap) {
+  const int n = kRingBudget / (cap * (int)(sizeof(float) + 1));
+  return n < 3 ? 3 : n > kMaxRing ? kMaxRing : n;
+}
+
+// dynamic shared memory of the sweep kernel
+inline int sweep_smem_bytes(int cap, int nring) { return nring * cap * (int)(sizeof(float) + 1); }
 
 struct QDev {
   Lattice lat;
@@ -85,10 +98,12 @@ struct Ctx {
   unsigned long long* n_done;  // finished configurations
   unsigned int* ticks;
   unsigned int* arrive;        // control blocks finished this tick
+  unsigned int* next_unit;     // next unit of this tick's sweep
   int* error;
   unsigned int max_ticks;
   cudaGraphConditionalHandle cond;
   int seg_cap;                  // floats per shared-memory ring slot of the FP units
+  int nring;                    // ring slots (3 .. kMaxRing)
   int use_cond;                 // set the WHILE condition at the end of a tick
   int server;                   // 1: slots are bound to a query by the host
   char** slot_base;             // [K] state of each slot (server mode)
@@ -274,6 +289,7 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
     *x.n_done = 0ull;
     *x.ticks = 0u;
     *x.arrive = 0u;
+    *x.next_unit = 0u;
     *x.error = 0;
   }
   __threadfence();
@@ -282,16 +298,32 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
 }
 
 
+// Ring state carried across the FP units of one CTA.
+struct Ring {
+  uint32_t ph;    // expected parity of each slot's barrier (identical in all threads)
+  uint32_t pend;  // thread 0: slots with a copy issued and not yet waited for
+  int base;       // slot of the next unit's first plane (identical in all threads)
+  bool dead;      // this thread saw a wait expire: no further waits or copies
+};
+
 // One FP unit: strips [k0, k0 + kCols) (one per thread) over layers
-// [t0, t1).  Layer t reads planes t+1, t+2, t+3; the segment [lo, hi) of each
-// plane the chunk touches is copied into ring slot (plane mod kRing) by one
-// thread (cp.async.bulk, mbarrier completion), kRing - 1 planes ahead of its
-// use.  ph holds the expected parity of each slot's barrier (identical in all
-// threads).
+// [t0, t1).  Layer t reads planes t+2, t+3 of nu and layer t of the degrees
+// (planes t+1 and older are already in registers).  The segment [lo, hi) of
+// each plane the chunk touches, and the same byte range of the degree layer
+// three planes below it, are copied into the next ring slot by thread 0
+// (cp.async.bulk; an mbarrier per slot counts the bytes).  Planes take ring
+// slots in the order they are copied, continuing across units: plane t0+1 of
+// this unit is in slot rg.base.  After each layer a block barrier frees the
+// slot of plane t+2 and thread 0 refills it with plane t+2+nring, so the
+// copies run nring-1 layers ahead of their use.  A wait that expires sets
+// error bit 2 and *abort; the thread then skips all further waits and
+// copies, and the kernel drains the copies in flight and returns after the
+// unit.
 __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat, const SlotView& v, bool odd,
-                                               int k0, int t0, int t1, float* ring, uint64_t* bars,
-                                               uint32_t& ph, const float* inv, int* s_red) {
-  const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap;
+                                               int k0, int t0, int t1, float* ring, uint8_t* dring,
+                                               uint64_t* full, Ring& rg, int* abort, const float* inv,
+                                               int* s_red) {
+  const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap, nring = x.nring;
   const int k = k0 + tid;
   const bool have = k < lat.n_strips;
   int b = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
@@ -313,8 +345,9 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   __syncthreads();
   if ((tid & 31) == 0) { atomicMin(&s_red[0], lo); atomicMax(&s_red[1], hi); }
   __syncthreads();
-  const int lo_al = s_red[0] & ~3;
-  int seg = ((s_red[1] + 3) & ~3) - lo_al;
+  // 16-entry alignment: 16-byte aligned copies of both the FP32 and the byte planes
+  const int lo_al = s_red[0] & ~15;
+  int seg = ((s_red[1] + 15) & ~15) - lo_al;
   if (seg > cap) {  // cannot happen: the host sized the ring for every lattice
     if (tid == 0) atomicOr(x.error, 4);
     seg = cap;
@@ -322,91 +355,112 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   const float* src = odd ? v.nu0 : v.nu1;
   float* dst = odd ? v.nu1 : v.nu0;
   const int last = t1 + 2;
-  auto issue = [&](int pl) {
-    if (tid == 0 && pl <= last) {
-      const int sl = pl % kRing;
-      fence_proxy_async_shared();
-      mbar_arrive_expect_tx(&bars[sl], (unsigned)seg * 4u);
-      bulk_g2s(ring + (size_t)sl * cap, src + (size_t)pl * P + lo_al, (unsigned)seg * 4u, &bars[sl]);
+  auto inc = [nring](int s) { return s + 1 == nring ? 0 : s + 1; };
+  // thread 0: copy plane pl (and the degree layer pl - 3) into slot sl
+  auto issue = [&](int pl, int sl) {
+    if (tid != 0 || rg.dead || pl > last) return;
+    rg.pend |= 1u << sl;
+    const int lay = pl - 3;
+    const bool with_dg = lay >= t0;
+    fence_proxy_async_shared();
+    mbar_arrive_expect_tx(&full[sl], (unsigned)seg * (with_dg ? 5u : 4u));
+    bulk_g2s(ring + (size_t)sl * cap, src + (size_t)pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
+    if (with_dg) bulk_g2s(dring + (size_t)sl * cap, v.dg + (size_t)lay * P + lo_al, (unsigned)seg, &full[sl]);
+  };
+  auto wait = [&](int sl) {
+    if (rg.dead) return;
+    if (!mbar_wait(&full[sl], (rg.ph >> sl) & 1u)) {
+      rg.dead = true; *abort = 1; atomicOr(x.error, 2);
+      return;
     }
+    rg.ph ^= 1u << sl;
+    rg.pend &= ~(1u << sl);
   };
-  auto wait = [&](int pl) {
-    const int sl = pl % kRing;
-    if (!mbar_wait(&bars[sl], (ph >> sl) & 1u) && tid == 0) atomicOr(x.error, 2);
-    ph ^= 1u << sl;
-  };
-  auto slot = [&](int pl) { return ring + (size_t)(pl % kRing) * cap; };
   const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
-  const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al;
+  const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al, g0 = b - lo_al;
 
-  for (int i = 1; i <= kRing; ++i) issue(t0 + i);
-  wait(t0 + 1);
-  wait(t0 + 2);
+  {
+    int sl = rg.base;
+    for (int i = 1; i <= nring; ++i, sl = inc(sl)) issue(t0 + i, sl);
+  }
+  const int s1 = rg.base;  // plane t0 + 1
+  int s2 = inc(s1);        // plane t + 2
+  int s3 = inc(s2);        // plane t + 3
+  wait(s1);
+  wait(s2);
   float up2 = 0.f, dp2 = 0.f, cp[4] = {0.f, 0.f, 0.f, 0.f};
   Runs A, B;
   if (have) {
-    const float* pl = slot(t0 + 1);
+    const float* pl = ring + (size_t)s1 * cap;
     up2 = pl[u0 + 2]; dp2 = pl[d0 + 2];
 #pragma unroll
     for (int i = 0; i < 4; ++i) cp[i] = pl[c0 + i];
-    load_runs(A, slot(t0 + 2), u0, d0, c0);
+    load_runs(A, ring + (size_t)s2 * cap, u0, d0, c0);
   }
-  __syncthreads();  // plane t0+1's slot is free
-  issue(t0 + kRing + 1);
-  // degrees are read from HBM one layer ahead of their use
-  const uint8_t* dgb = v.dg + b;
-  int g0 = 0, g1 = 0, g2 = 0;
-  if (have) { const uint8_t* d = dgb + (size_t)t0 * P; g0 = d[0]; g1 = d[1]; g2 = d[2]; }
+  __syncthreads();  // plane t0 + 1's slot is free
+  issue(t0 + 1 + nring, s1);
   int t = t0;
   for (;;) {
-    int h0 = 0, h1 = 0, h2 = 0;
-    if (have && t + 1 < t1) { const uint8_t* d = dgb + (size_t)(t + 1) * P; h0 = d[0]; h1 = d[1]; h2 = d[2]; }
-    wait(t + 3);
+    wait(s3);
     if (have) {
-      load_runs(B, slot(t + 3), u0, d0, c0);
-      strip_emit_deg(A, B, up2, dp2, cp, slot(t + 2), e0, f0, dst + (size_t)(t + 2) * P, b,
-                     g0, g1, g2, inv);
+      load_runs(B, ring + (size_t)s3 * cap, u0, d0, c0);
+      const uint8_t* dg = dring + (size_t)s3 * cap + g0;
+      strip_emit_deg(A, B, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
+                     dg[0], dg[1], dg[2], inv);
       up2 = A.U[2]; dp2 = A.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
     }
-    g0 = h0; g1 = h1; g2 = h2;
-    __syncthreads();  // plane t+2's slot is free
-    issue(t + kRing + 2);
+    __syncthreads();  // plane t + 2's slot is free
+    issue(t + 2 + nring, s2);
+    s2 = s3; s3 = inc(s3);
     if (++t >= t1) break;
-    if (have && t + 1 < t1) { const uint8_t* d = dgb + (size_t)(t + 1) * P; h0 = d[0]; h1 = d[1]; h2 = d[2]; }
-    wait(t + 3);
+    wait(s3);
     if (have) {
-      load_runs(A, slot(t + 3), u0, d0, c0);
-      strip_emit_deg(B, A, up2, dp2, cp, slot(t + 2), e0, f0, dst + (size_t)(t + 2) * P, b,
-                     g0, g1, g2, inv);
+      load_runs(A, ring + (size_t)s3 * cap, u0, d0, c0);
+      const uint8_t* dg = dring + (size_t)s3 * cap + g0;
+      strip_emit_deg(B, A, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
+                     dg[0], dg[1], dg[2], inv);
       up2 = B.U[2]; dp2 = B.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
     }
-    g0 = h0; g1 = h1; g2 = h2;
     __syncthreads();
-    issue(t + kRing + 2);
+    issue(t + 2 + nring, s2);
+    s2 = s3; s3 = inc(s3);
     if (++t >= t1) break;
   }
+  // s2 now holds plane t1 + 2 (the last); the next unit continues after it
+  rg.base = inc(s2);
 }
 
 __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
-  extern __shared__ __align__(128) float ring[];  // kRing slots of x.seg_cap floats
+  // x.nring slots of x.seg_cap floats (nu planes), then x.nring of x.seg_cap bytes (degrees)
+  extern __shared__ __align__(128) float ring[];
+  uint8_t* dring = reinterpret_cast<uint8_t*>(ring + (size_t)x.nring * x.seg_cap);
   __shared__ float inv_deg[16];
   __shared__ uint32_t s_flag;
   __shared__ int s_red[2];
-  __shared__ __align__(8) uint64_t bars[kRing];
+  __shared__ __align__(8) uint64_t bars[kMaxRing];  // one per ring slot
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
   if (tid < 16) inv_deg[tid] = tid ? __frcp_rn((float)tid) : 0.f;
   if (tid == 0) {
-    for (int i = 0; i < kRing; ++i) mbar_init(&bars[i], 1);
+    s_abort = 0;
+    for (int i = 0; i < x.nring; ++i) mbar_init(&bars[i], 1);  // one arrival plus the bytes
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t ph = 0;  // expected parity per ring slot
+  Ring rg{0u, 0u, 0, false};
   const int total = x.pre[x.K];
-  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+  // units are taken from a tick-wide counter (double-buffered broadcast: one
+  // block barrier per unit)
+  __shared__ int s_unit[2];
+  for (int it = 0;; ++it) {
+    if (tid == 0) s_unit[it & 1] = (int)atomicAdd(x.next_unit, 1u);
+    __syncthreads();
+    const int u = s_unit[it & 1];
+    if (u >= total) break;
     // slot: last s with pre[s] <= u (binary search)
     int lo = 0, hi = x.K - 1;
     while (lo < hi) {
@@ -429,13 +483,24 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
     if (kind == U_FP) {
       const int t0 = p.lo[U_FP] + rchunk * kRowsFP;
       const int t1 = min(t0 + kRowsFP, p.hi[U_FP]);
-      fp_unit_staged(x, lat, v, (c.m & 1) != 0, cchunk * kCols, t0, t1, ring, bars, ph, inv_deg, s_red);
+      fp_unit_staged(x, lat, v, (c.m & 1) != 0, cchunk * kCols, t0, t1, ring, dring, bars, rg, &s_abort,
+                     inv_deg, s_red);
+      __syncthreads();
+      if (s_abort) {  // a wait expired: let the copies in flight land (bounded), then stop
+        if (tid == 0)
+          for (int sl = 0; sl < x.nring; ++sl)
+            if ((rg.pend >> sl) & 1u) mbar_wait(&bars[sl], (rg.ph >> sl) & 1u);
+        return;
+      }
     } else if (kind == U_BITS) {
       const int w0 = p.lo[U_BITS] + rchunk * kRows;
       const int w1 = min(w0 + kRows, p.hi[U_BITS]);
       const bool odd = (c.m & 1) != 0;
-      const uint32_t* Rs = odd ? v.R0 : v.R1;
-      uint32_t* Rd = odd ? v.R1 : v.R0;
+      // Rs and occw are only read during a sweep (no unit of this tick writes
+      // the rows read here): read-only cache path
+      const uint32_t* __restrict__ Rs = odd ? v.R0 : v.R1;
+      uint32_t* __restrict__ Rd = odd ? v.R1 : v.R0;
+      const uint32_t* __restrict__ occw = v.occw;
       uint32_t fl = 0;
       if (a < A) {
         const int sg = lat.sigma[a];
@@ -443,13 +508,24 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
 #pragma unroll
         for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
         const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
+#pragma unroll 2
         for (int tw = w0; tw < w1; ++tw) {
-          uint32_t acc = shifted_word(Rs, S, a, tw, -1) | shifted_word(Rs, S, a, tw, 1);
+          const uint32_t* r0 = Rs + (size_t)tw * S;  // word tw - 1
+          const uint32_t* r1 = r0 + S;               // word tw
+          const uint32_t* r2 = r1 + S;               // word tw + 1
+          const uint32_t old = __ldg(r1 + a);
+          // end contacts: tubes t-1 and t+1 of the own column
+          uint32_t acc = ((old << 1) | (__ldg(r0 + a) >> 31)) | ((old >> 1) | (__ldg(r2 + a) << 31));
 #pragma unroll
-          for (int d = 0; d < kLateral; ++d) acc |= shifted_word(Rs, S, nb[d], tw, dir_dt(d, sg));
+          for (int d = 0; d < kLateral; ++d) {
+            const int dt = dir_dt(d, sg);
+            uint32_t w = __ldg(r1 + nb[d]);
+            if (dt > 0) w = (w >> 1) | (__ldg(r2 + nb[d]) << 31);
+            else if (dt < 0) w = (w << 1) | (__ldg(r0 + nb[d]) >> 31);
+            acc |= w;
+          }
           const int wi = (tw + 1) * S + a;
-          const uint32_t old = Rs[wi];
-          const uint32_t nw = old | (acc & v.occw[wi]);
+          const uint32_t nw = old | (acc & __ldg(occw + wi));
           Rd[wi] = nw;
           if (nw != old) fl |= kGrow;
           if (tw == endw && (((nw & ~old) >> endb) & 1u)) fl |= kEnd;
@@ -535,6 +611,21 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
       }
     }
   }
+}
+
+// Persistent sweep grid: as many CTAs as fit on the device at once (units
+// are fetched dynamically, so more CTAs would only add start-up work).
+int sweep_grid(const Ctx& x) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, kCols,
+                                                    sweep_smem_bytes(x.seg_cap, x.nring)) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return nsm * per_sm;
 }
 
 __device__ inline float block_sum_f(float v, float* red) {
@@ -660,9 +751,11 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
   plan_prefix(x);
   if (tid == 0) {
     *x.arrive = 0u;
+    *x.next_unit = 0u;
     const unsigned t = *x.ticks + 1u;
     *x.ticks = t;
-    const bool more = *x.n_done < (unsigned long long)x.n_items;
+    // an error bit (expired wait, failed check) ends the loop at once
+    const bool more = *x.n_done < (unsigned long long)x.n_items && *x.error == 0;
     if (x.use_cond) {
       if (more && t >= x.max_ticks) *x.error = 1;
       cudaGraphSetConditional(x.cond, (more && t < x.max_ticks) ? 1u : 0u);
@@ -729,15 +822,17 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   x.ticks = (unsigned int*)(x.work + 2);
   x.arrive = x.ticks + 1;
   x.error = (int*)(x.ticks + 2);
+  x.next_unit = x.ticks + 3;
   q += 256;
   x.pool = q;
   x.slot_bytes = slot;
   x.use_cond = 0; x.server = 0; x.slot_base = nullptr; x.qnext = nullptr; x.qdone = nullptr;
   {
-    int cap = 4;
-    for (int i = 0; i < nq; ++i) cap = std::max(cap, max_segment(qs[i].lat.W, kCols) + 8);
+    int cap = 16;
+    for (int i = 0; i < nq; ++i) cap = std::max(cap, max_segment(qs[i].lat.W, kCols) + 16);
     x.seg_cap = cap;
-    const int bytes = kRing * cap * (int)sizeof(float);
+    x.nring = ring_depth(cap);
+    const int bytes = sweep_smem_bytes(cap, x.nring);
     cudaError_t ea = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (ea != cudaSuccess) { cudaFreeAsync(P->mem, st); delete P; return cuda_fail(ea, "sweep smem"); }
   }
@@ -757,10 +852,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   // pool must start zeroed: padding rows / sentinel columns are never written
   if (e == cudaSuccess) e = cudaMemsetAsync(x.pool, 0, (size_t)K * slot, st);
   if (e != cudaSuccess) { cudaFreeAsync(P->mem, st); delete P; return cuda_fail(e, "stream plan init"); }
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  P->grid = nsm * 8;
+  P->grid = sweep_grid(x);
   *out = P;
   return PC_OK;
 }
@@ -788,7 +880,7 @@ pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* d
   cudaKernelNodeParams sp = {};
   sp.func = (void*)sweep_kernel;
   sp.gridDim = dim3(P->grid); sp.blockDim = dim3(kCols); sp.kernelParams = args;
-  sp.sharedMemBytes = (unsigned)(kRing * x.seg_cap * sizeof(float));
+  sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring);
   cudaGraphNode_t n_sweep, n_ctl;
   PC_CUDA(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &sp));
   cudaKernelNodeParams cpk = {};
@@ -848,7 +940,7 @@ __global__ void server_reset_kernel(Ctx x) {
     x.ctl[s] = c;
     x.pre[s] = 0;
   }
-  if (threadIdx.x == 0) { x.pre[x.K] = 0; *x.arrive = 0u; *x.ticks = 0u; *x.n_done = 0ull; }
+  if (threadIdx.x == 0) { x.pre[x.K] = 0; *x.arrive = 0u; *x.next_unit = 0u; *x.ticks = 0u; *x.n_done = 0ull; }
 }
 
 __global__ void server_status_kernel(Ctx x, int* phases) {
@@ -867,7 +959,7 @@ struct ServerEngine {
   int max_queries = 0;
 };
 
-pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk,
+pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chunk, int max_W,
                                cudaStream_t st, ServerEngine** out) {
   *out = nullptr;
   ServerEngine* E = new ServerEngine();
@@ -894,9 +986,11 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
   x.ticks = (unsigned int*)(x.work + 2);
   x.arrive = x.ticks + 1;
   x.error = (int*)(x.ticks + 2);
+  x.next_unit = x.ticks + 3;
   x.pool = nullptr; x.slot_bytes = 0; x.max_ticks = 0xffffffffu;
   x.use_cond = 0; x.server = 1;
-  x.seg_cap = max_segment(255, kCols) + 8;  // any lattice the server accepts
+  x.seg_cap = max_segment(max_W, kCols) + 16;  // any lattice the server accepts
+  x.nring = ring_depth(x.seg_cap);
   E->max_queries = nq;
   pc_status rc = PC_OK;
   do {
@@ -909,7 +1003,7 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kRing * x.seg_cap * (int)sizeof(float))) != cudaSuccess) {
+                                  sweep_smem_bytes(x.seg_cap, x.nring))) != cudaSuccess) {
       rc = cuda_fail(e, "sweep smem"); break;
     }
     cudaGraph_t g;
@@ -918,9 +1012,9 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     cudaGraphNode_t prev = nullptr;
     for (int t = 0; t < std::max(1, ticks_per_chunk) && rc == PC_OK; ++t) {
       cudaKernelNodeParams sp = {};
-      sp.func = (void*)sweep_kernel; sp.gridDim = dim3(nsm * 8); sp.blockDim = dim3(kCols);
+      sp.func = (void*)sweep_kernel; sp.gridDim = dim3(sweep_grid(x)); sp.blockDim = dim3(kCols);
       sp.kernelParams = args;
-      sp.sharedMemBytes = (unsigned)(kRing * x.seg_cap * sizeof(float));
+      sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring);
       cudaGraphNode_t ns, nc;
       if ((e = cudaGraphAddKernelNode(&ns, g, prev ? &prev : nullptr, prev ? 1 : 0, &sp)) != cudaSuccess) { rc = cuda_fail(e, "node"); break; }
       cudaKernelNodeParams cp = {};
@@ -1012,12 +1106,15 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st) {
     unsigned long long done = 0;
     for (int chunk = 0; rc == PC_OK && done < (unsigned long long)x.n_items; ++chunk) {
       for (int i = 0; i < 32; ++i) {
-        sweep_kernel<<<P->grid, kCols, kRing * x.seg_cap * sizeof(float), st>>>(x);
+        sweep_kernel<<<P->grid, kCols, sweep_smem_bytes(x.seg_cap, x.nring), st>>>(x);
         control_kernel<<<x.K, kCols, 0, st>>>(x);
       }
+      int err = 0;
       cudaError_t e = cudaMemcpyAsync(&done, x.n_done, 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&err, x.error, sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) rc = cuda_fail(e, "host loop");
+      else if (err) { set_error("streamed solver: device error flag set"); rc = (err & 2) ? PC_ERR_TIMEOUT : PC_ERR_INTERNAL; }
       if ((unsigned long long)chunk * 32 > x.max_ticks) { set_error("streamed solver did not converge"); rc = PC_ERR_INTERNAL; }
     }
     stream_plan_release(P, st);

@@ -35,30 +35,17 @@ __device__ __forceinline__ void load_runs(Runs& R, const float* __restrict__ pl,
   for (int i = 0; i < 5; ++i) R.C[i] = pl[c0 + i];
 }
 
-// Site updates of layer t for one strip: c = runs of layer t, n = layer t+1;
-// (up2, dp2, cp) = the layer t-1 values the sublattice-0 site needs.
-__device__ __forceinline__ void strip_emit(const Runs& c, const Runs& n, float up2, float dp2,
-                                           const float (&cp)[4], const float* __restrict__ plc,
-                                           int e0, int f0, float* __restrict__ out_pl, int b,
-                                           const uint8_t* __restrict__ dgl,
-                                           const float* __restrict__ inv) {
-  const float e_0 = plc[e0], e_1 = plc[e0 + 1], e_2 = plc[e0 + 2];
-  const float f_0 = plc[f0], f_1 = plc[f0 + 1], f_2 = plc[f0 + 2];
-  // sublattice 0: layer-below neighbours at t-1, layer-above ones at t
-  const float s0 = c.U[3] + c.U[0] + c.U[1] + up2 + c.D[0] + c.D[3] + c.D[1] + dp2 +
-                   c.C[2] + cp[0] + cp[1] + n.C[1] + e_0 + f_0;
-  // sublattice 1: all in tube t (end contacts at t +- 1)
-  const float s1 = c.U[4] + c.U[1] + c.U[2] + c.U[3] + c.D[1] + c.D[4] + c.D[2] + c.D[3] +
-                   c.C[3] + c.C[1] + cp[2] + n.C[2] + e_1 + f_1;
-  // sublattice 2: layer-above neighbours at t+1, layer-below ones at t
-  const float s2 = c.U[5] + c.U[2] + n.U[3] + c.U[4] + c.D[2] + c.D[5] + n.D[3] + c.D[4] +
-                   n.C[4] + c.C[2] + cp[3] + n.C[3] + e_2 + f_2;
-  out_pl[b] = inv[dgl[b]] * s0;
-  out_pl[b + 1] = inv[dgl[b + 1]] * s1;
-  out_pl[b + 2] = inv[dgl[b + 2]] * s2;
+// Sum of 14 terms as a balanced tree (depth 4 instead of a 13-add chain).
+__device__ __forceinline__ float sum14(float a0, float a1, float a2, float a3, float a4, float a5, float a6,
+                                       float a7, float a8, float a9, float a10, float a11, float a12,
+                                       float a13) {
+  return (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) +
+         (((a8 + a9) + (a10 + a11)) + (a12 + a13));
 }
 
-// As strip_emit, with the three degrees given (prefetched by the caller).
+// Site updates of layer t for one strip: c = runs of layer t, n = layer t+1;
+// (up2, dp2, cp) = the layer t-1 values the sublattice-0 site needs; g0..g2
+// the degrees of the three sites.
 __device__ __forceinline__ void strip_emit_deg(const Runs& c, const Runs& n, float up2, float dp2,
                                                const float (&cp)[4], const float* __restrict__ plc,
                                                int e0, int f0, float* __restrict__ out_pl, int b,
@@ -66,15 +53,27 @@ __device__ __forceinline__ void strip_emit_deg(const Runs& c, const Runs& n, flo
                                                const float* __restrict__ inv) {
   const float e_0 = plc[e0], e_1 = plc[e0 + 1], e_2 = plc[e0 + 2];
   const float f_0 = plc[f0], f_1 = plc[f0 + 1], f_2 = plc[f0 + 2];
-  const float s0 = c.U[3] + c.U[0] + c.U[1] + up2 + c.D[0] + c.D[3] + c.D[1] + dp2 +
-                   c.C[2] + cp[0] + cp[1] + n.C[1] + e_0 + f_0;
-  const float s1 = c.U[4] + c.U[1] + c.U[2] + c.U[3] + c.D[1] + c.D[4] + c.D[2] + c.D[3] +
-                   c.C[3] + c.C[1] + cp[2] + n.C[2] + e_1 + f_1;
-  const float s2 = c.U[5] + c.U[2] + n.U[3] + c.U[4] + c.D[2] + c.D[5] + n.D[3] + c.D[4] +
-                   n.C[4] + c.C[2] + cp[3] + n.C[3] + e_2 + f_2;
+  // sublattice 0: layer-below neighbours at t-1, layer-above ones at t
+  const float s0 = sum14(c.U[3], c.U[0], c.U[1], up2, c.D[0], c.D[3], c.D[1], dp2, c.C[2], cp[0],
+                         cp[1], n.C[1], e_0, f_0);
+  // sublattice 1: all in tube t (end contacts at t +- 1)
+  const float s1 = sum14(c.U[4], c.U[1], c.U[2], c.U[3], c.D[1], c.D[4], c.D[2], c.D[3], c.C[3],
+                         c.C[1], cp[2], n.C[2], e_1, f_1);
+  // sublattice 2: layer-above neighbours at t+1, layer-below ones at t
+  const float s2 = sum14(c.U[5], c.U[2], n.U[3], c.U[4], c.D[2], c.D[5], n.D[3], c.D[4], n.C[4],
+                         c.C[2], cp[3], n.C[3], e_2, f_2);
   out_pl[b] = inv[g0] * s0;
   out_pl[b + 1] = inv[g1] * s1;
   out_pl[b + 2] = inv[g2] * s2;
+}
+
+// As strip_emit_deg, with the degrees read from the layer's degree plane dgl.
+__device__ __forceinline__ void strip_emit(const Runs& c, const Runs& n, float up2, float dp2,
+                                           const float (&cp)[4], const float* __restrict__ plc,
+                                           int e0, int f0, float* __restrict__ out_pl, int b,
+                                           const uint8_t* __restrict__ dgl,
+                                           const float* __restrict__ inv) {
+  strip_emit_deg(c, n, up2, dp2, cp, plc, e0, f0, out_pl, b, dgl[b], dgl[b + 1], dgl[b + 2], inv);
 }
 
 // Layers [t0, t1) of the strip at plane position b.  Layer t of nu is the

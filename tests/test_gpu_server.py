@@ -120,3 +120,22 @@ def test_errors_busy_cancel_and_oversize():
         assert e.value.status == pc.PC_ERR_ARG
     finally:
         srv.close()  # remaining queued tickets are cancelled
+
+
+def test_max_width_bounds_streamed_queries():
+    # the staging ring is sized for max_W: wider HBM-slot lattices are refused,
+    # resident ones of any accepted width still run
+    srv = pc.Server(hbm_budget_bytes=256 << 20, max_slots=8, max_slots_per_query=8, ticks_per_poll=2,
+                    max_W=8)
+    try:
+        with pytest.raises(pc.PercolError) as e:
+            srv.submit((12, 400, 0.3, 1, 0, 4))
+        assert e.value.status == pc.PC_ERR_ARG
+        specs = [(8, 300, 0.25, 3, 0, 16), (4, 16, 0.2, 3, 0, 40)]
+        tickets = [srv.submit(sp) for sp in specs]
+        for sp, t in zip(specs, tickets):
+            r = srv.poll(t, timeout_s=120.0)
+            assert r is not None
+            _same(r, pc.pc_inspect(*sp), sp)
+    finally:
+        srv.close()
