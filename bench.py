@@ -182,6 +182,8 @@ def run_reference(args):
 # method's data: nu read 4 B + nu write 4 B + occupancy 1/8 B + reached-set
 # bit read and write 1/4 B (the per-unit figure of the measurement plan).
 HBM_BYTES_PER_SU = 8.375
+# bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
+BITS_BYTES_PER_SU = 0.375
 
 
 def batching_specs(n=10_000):
@@ -192,13 +194,13 @@ def run_large(args, pc, torch):
     """W = 64, L = 4096 (51.1 M sites), p in {0.14, 0.1533, 0.17}, 64
     configurations each, seed 4: the streamed solver, HBM bound."""
     Wl, Ll, seed, n = 64, 4096, 4, args.large_configs
-    ps = [0.14, 0.1533, 0.17]
+    ps = [0.14, 0.1533, 0.17] if args.large_p is None else [float(v) for v in args.large_p.split(",")]
     A = 3 * Wl * (Wl + 1) + 1
     stream = torch.cuda.current_stream()
     outs = [pc._alloc_outputs(n, True, pc.ALL_OUTPUTS) for _ in ps]
     for _ in range(args.warmup):  # warm-up on one configuration per p
         for p in ps:
-            pc.pc_inspect(Wl, Ll, p, seed, 0, 1, device=True, stream=stream)
+            pc.pc_inspect(Wl, Ll, p, seed, 0, 1, device=True, stream=stream, bits_only=args.bits_only)
     torch.cuda.synchronize()
     times = []
     with Clocks(0) as clk:
@@ -206,33 +208,50 @@ def run_large(args, pc, torch):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             ev[0].record(stream)
             for i, p in enumerate(ps):
-                pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=True, out=outs[i], stream=stream)
+                pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=True, out=outs[i], stream=stream,
+                              bits_only=args.bits_only)
             ev[1].record(stream)
             torch.cuda.synchronize()
             times.append(ev[0].elapsed_time(ev[1]) / 1e3)
     su = 0
     perc = []
+    ticks = 0
     for o in outs:
         h = {k: v.cpu().numpy() for k, v in o.items()}
         su += site_updates(A, Ll, h["verdict"], h["first_hit"], h["m_stop"])
         perc.append(int(h["verdict"].sum()))
+        steps = np.where(h["verdict"] != 0, h["first_hit"] - 1, h["m_stop"])
+        # one wave of slots: draw + prepare ticks, then one tick per step
+        ticks += int(steps.max(initial=0)) + 3
     t = float(np.mean(times))
+    # end to end through the public call with host outputs (D2H inside)
+    t0 = time.perf_counter()
+    for p in ps:
+        pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=False, bits_only=args.bits_only)
+    e2e_t = time.perf_counter() - t0
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = HBM_BYTES_PER_SU * su / t / 1e9
+    bps = BITS_BYTES_PER_SU if args.bits_only else HBM_BYTES_PER_SU
+    achieved = bps * su / t / 1e9
     return {
         "metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"large W=64 L=4096 p=0.14/0.1533/0.17 x {n} configs seed=4",
+        "config": {"workload": f"large W=64 L=4096 p={'/'.join(str(p) for p in ps)} x {n} configs seed=4"
+                               + (" (bits only)" if args.bits_only else ""),
                    "site_updates_per_step": su, "percolating_per_p": perc, "solver": "streamed",
                    "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB)"},
         "configs_per_s": n * len(ps) / t,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
-                     "model": f"{HBM_BYTES_PER_SU} B/site-update x site-updates / time of the whole "
+                     "model": f"{bps} B/site-update x site-updates / time of the whole "
                               "solve (sweep + control kernels), peak = measured copy bandwidth"},
         "clocks": clk.summary(),
+        "e2e": {"value": su / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": len(ps) * (n * (1 + 4 + 4 + 4) + 8)},
+        # kernel nodes run by the streamed solver's graphs: a sweep and a
+        # control kernel per tick, plus the query upload and init kernels
+        "gpu_launches": 2 * ticks + 2 * len(ps),
     }
 
 
@@ -268,6 +287,30 @@ def run_batch(args, pc, torch):
     with Clocks(0) as clk:
         tb = timed(batched, args.steps)
         tp = timed(plain, args.steps)
+    # where the plain time goes: each per-size launch timed alone
+    per_query_ms = {}
+    for sp, o in zip(specs, plain_outs):
+        W_, L_, p_, seed_, b_, n_ = sp
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pc.pc_inspect(W_, L_, p_, seed_, b_, n_, device=True, out=o, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_query_ms[f"{W_},{L_}"] = round(e0.elapsed_time(e1), 3)
+    # a naive GPU path for contrast: one configuration per launch, on a
+    # sample of each size's configurations (extrapolated per configuration)
+    n_one = 8
+    t_one = 0.0
+    one = pc._alloc_outputs(1, True, pc.ALL_OUTPUTS)
+    for sp in specs:
+        W_, L_, p_, seed_, b_, n_ = sp
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in range(n_one):
+            pc.pc_inspect(W_, L_, p_, seed_, b_ + c, 1, device=True, out=one, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_one += e0.elapsed_time(e1) / 1e3 / n_one * n_
     su, n_tot, same = 0, 0, True
     for sp, o, po in zip(specs, outs, plain_outs):
         W_, L_ = sp[0], sp[1]
@@ -285,6 +328,9 @@ def run_batch(args, pc, torch):
                    "queries": len(specs), "configs_per_query": args.batch_configs,
                    "l2": "no flush (per-launch working sets differ; see plain)"},
         "plain_configs_per_s": n_tot / tp, "batched_over_plain": tp / tb,
+        "plain_ms_per_query": per_query_ms,
+        "one_config_per_launch": {"configs_per_s": n_tot / t_one, "batched_over": t_one / tb,
+                                  "sample": f"first {n_one} configurations of each size, extrapolated"},
         "site_updates_per_s_batched": su / tb, "results_identical": bool(same),
         "clocks": clk.summary(),
     }
@@ -393,7 +439,16 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--large-configs", type=int, default=64)
     ap.add_argument("--batch-configs", type=int, default=10_000)
+    ap.add_argument("--bits-only", action="store_true",
+                    help="verdicts only (PC_BITS_ONLY): the reached-set propagation without the FP32 recursion")
+    ap.add_argument("--large-p", default=None,
+                    help="comma list of p for the large workload (a profiling subset)")
+    ap.add_argument("--only-p", type=float, default=None,
+                    help="p-sweep at this one p (a profiling subset, not the benchmark workload)")
     args = ap.parse_args()
+    global PS
+    if args.only_p is not None:
+        PS = [args.only_p]
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "psweep":
@@ -492,7 +547,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "p-sweep W=8 L=64 p=0.100..0.200/0.005 seed=2",
+        "config": {"workload": ("p-sweep W=8 L=64 p=0.100..0.200/0.005 seed=2" if len(PS) > 1 else
+                                f"p-sweep subset W=8 L=64 p={PS[0]} seed=2"),
                    "W": W, "L": L, "n_p": len(PS), "configs_per_p": n_cfg,
                    "configs_per_step": n_cfg * len(PS) * world,
                    "site_updates_per_step_per_gpu": su_step,

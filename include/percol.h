@@ -68,6 +68,13 @@ typedef int32_t pc_status;
                                   are device pointers; Pi must be NULL */
 #define PC_MODE_RESIDENT 0x10  /* force the shared-memory resident solver */
 #define PC_MODE_STREAM 0x20    /* force the streamed (global memory) solver */
+#define PC_BITS_ONLY 0x40      /* verdicts only: propagate the exact reached set
+                                  alone and skip the FP32 recursion.  The
+                                  method needs only whether the detector
+                                  probability is zero (Sec. II.B), which the
+                                  reached set decides exactly; verdicts,
+                                  first_hit, m_stop and n_percolating equal the
+                                  full inspection's, mass is written 0 */
 
 /*
  * Lattice size (Sec. II.A): n_columns = A = 3W(W+1)+1, n_sites = A*L.
@@ -86,6 +93,21 @@ pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed,
                        uint32_t* occ_bits, void* cuda_stream);
 
 /*
+ * Fixed-count occupancy (Sec. II.A: a random permutation of the N sites puts
+ * exactly n_metallic = Np of them metallic), in the layout of pc_occupancy.
+ * Site i carries the key (u_i << 32) | i, u_i its 32-bit word of the
+ * Bernoulli stream above; the Np sites with the smallest keys are metallic (a
+ * uniformly random Np-subset; it equals the Bernoulli configuration at p
+ * whenever Np is that configuration's metallic count).  Inspect the result
+ * with pc_inspect_occupancy.  Synchronises cuda_stream (a convergence check).
+ * Errors: PC_ERR_ARG (n_metallic outside [0, N]), PC_ERR_CUDA,
+ * PC_ERR_INTERNAL.
+ */
+pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t seed,
+                             int64_t config_begin, int64_t n_configs,
+                             uint32_t* occ_bits, void* cuda_stream);
+
+/*
  * Inspect configurations config_begin .. +n_configs-1 at probability p
  * (Sec. II.B; Pi(p) of Sec. III).  Per-configuration outputs, each
  * [n_configs] and each optional except verdicts:
@@ -97,7 +119,8 @@ pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed,
  *   m_stop    : steps taken: first_hit if percolating, else the first step
  *               whose reached set did not grow; 0 if no start site is metallic
  * n_percolating (int64) and Pi (= n_percolating / n_configs) are optional.
- * Outputs are host pointers unless flags has PC_OUT_DEVICE.
+ * Outputs are host pointers unless flags has PC_OUT_DEVICE.  flags may also
+ * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, and PC_BITS_ONLY.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
  */
 pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed,
@@ -155,7 +178,8 @@ typedef struct pc_result {
  * environment variable PC_TUNE_FILE, if set).
  * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
- * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.
+ * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
+ * applies to every query of the batch.
  * Results equal those of pc_inspect on each query.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
  */

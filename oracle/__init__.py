@@ -66,13 +66,14 @@ def _load():
             lib.oracle_columns.argtypes = [i32, vp, vp, vp]
             lib.oracle_adjacency.argtypes = [i32, i32, vp, vp]
             lib.oracle_occupancy.argtypes = [i32, i32, dbl, u64, i64, i64, vp]
+            lib.oracle_site_words.argtypes = [i32, i32, u64, i64, i64, vp]
             lib.oracle_inspect.argtypes = [i32, i32, vp, dbl, u64, i64, i64, i32, i32,
                                            vp, vp, vp, vp, vp]
             lib.oracle_first_passage.argtypes = [i32, i32, vp, ctypes.c_int32, vp, vp]
             lib.oracle_first_passage_dense.argtypes = [i32, vp, i32, i32, i32, vp]
             lib.oracle_max_threads.argtypes = []
             for f in ("oracle_lattice_info", "oracle_columns", "oracle_adjacency",
-                      "oracle_occupancy", "oracle_inspect", "oracle_first_passage",
+                      "oracle_occupancy", "oracle_site_words", "oracle_inspect", "oracle_first_passage",
                       "oracle_first_passage_dense", "oracle_max_threads"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -138,6 +139,31 @@ def occupancy(W: int, L: int, p: float, seed: int, cfg0: int, n: int) -> np.ndar
     occ = np.zeros((n, N), np.uint8)
     _check(_load().oracle_occupancy(W, L, float(p), int(seed) & (2**64 - 1), cfg0, n,
                                     _ptr(occ)), "occupancy")
+    return occ
+
+
+def site_words(W: int, L: int, seed: int, cfg0: int, n: int) -> np.ndarray:
+    """The 32-bit random word of each site [n][N] (the Bernoulli draw's stream)."""
+    _, N = lattice_info(W, L)
+    w = np.zeros((n, N), np.uint32)
+    _check(_load().oracle_site_words(W, L, int(seed) & (2**64 - 1), cfg0, n, _ptr(w)), "site_words")
+    return w
+
+
+def occupancy_fixed(W: int, L: int, n_metallic: int, seed: int, cfg0: int, n: int) -> np.ndarray:
+    """Fixed-count occupancy bytes [n][N] (Sec. II.A: a random permutation of
+    the N sites puts exactly Np = n_metallic of them metallic).  The
+    permutation sorts the sites by their random word, ties by site index; the
+    first Np sites of it are metallic."""
+    _, N = lattice_info(W, L)
+    if not 0 <= n_metallic <= N:
+        raise ValueError("n_metallic must be in [0, N]")
+    words = site_words(W, L, seed, cfg0, n)
+    occ = np.zeros((n, N), np.uint8)
+    idx = np.arange(N)
+    for c in range(n):
+        order = np.lexsort((idx, words[c]))  # primary key: word, then index
+        occ[c, order[:n_metallic]] = 1
     return occ
 
 

@@ -532,6 +532,31 @@ int oracle_occupancy(int W, int L, double p, uint64_t seed, int64_t cfg0,
   return OR_OK;
 }
 
+/*
+ * The 32-bit random word of every site (words: [n][N]) of configurations
+ * cfg0..cfg0+n-1: the same counter stream as the Bernoulli draw above.  The
+ * fixed-count sample space of Sec. II.A (a random permutation of the sites
+ * puts exactly Np of them metallic) is built from these words by the Python
+ * wrapper: the metallic sites are the Np smallest keys (word, site index).
+ */
+int oracle_site_words(int W, int L, uint64_t seed, int64_t cfg0, int64_t n, uint32_t *words) {
+  if (check_args(W, L) || cfg0 < 0 || n < 0 || cfg0 + n > 4294967296LL) return OR_ERR_ARG;
+  int64_t N = oracle_n_columns(W) * (int64_t)L;
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (int64_t c = 0; c < n; ++c) {
+    uint32_t word[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < N; ++i) {
+      if ((i & 3) == 0) {
+        uint32_t ctr[4] = {(uint32_t)(i >> 2), (uint32_t)(cfg0 + c),
+                           (uint32_t)W | ((uint32_t)L << 8), 0u};
+        oracle_philox4x32_10(ctr, key, word);
+      }
+      words[c * N + i] = word[i & 3];
+    }
+  }
+  return OR_OK;
+}
+
 enum { MODE_MARKOV = 0, MODE_BFS = 1, MODE_UNIONFIND = 2, MODE_MARKOV_FULL = 3 };
 
 /*

@@ -28,6 +28,7 @@ PC_OUT_DEVICE = 0x1
 PC_ASYNC = 0x2
 PC_MODE_RESIDENT = 0x10
 PC_MODE_STREAM = 0x20
+PC_BITS_ONLY = 0x40
 
 _STATUS = {PC_ERR_ARG: "PC_ERR_ARG", PC_ERR_OOM: "PC_ERR_OOM", PC_ERR_CUDA: "PC_ERR_CUDA",
            PC_ERR_TIMEOUT: "PC_ERR_TIMEOUT", PC_ERR_BUSY: "PC_ERR_BUSY",
@@ -39,6 +40,7 @@ _i32, _i64, _u64, _dbl, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
 SIGNATURES = {
     "pc_lattice_info": [_i32, _i32, _vp, _vp],
     "pc_occupancy": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp],
+    "pc_occupancy_fixed": [_i32, _i32, _i64, _u64, _i64, _i64, _vp, _vp],
     "pc_inspect": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_occupancy": [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
     "pc_inspect_static": [_i32, _i32, _dbl, _u64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -149,6 +151,20 @@ def pc_occupancy(W: int, L: int, p: float, seed: int, config_begin: int, n_confi
     return out
 
 
+def pc_occupancy_fixed(W: int, L: int, n_metallic: int, seed: int, config_begin: int,
+                       n_configs: int, out=None, stream=None):
+    """Fixed-count occupancy (Sec. II.A: exactly n_metallic metallic sites per
+    configuration, a uniformly random subset), in pc_occupancy's layout."""
+    import torch
+    wpc = words_per_config(W, L)
+    if out is None:
+        out = torch.empty((n_configs, wpc), dtype=torch.int32, device="cuda")
+    assert out.is_cuda and out.is_contiguous() and out.numel() >= n_configs * wpc
+    _check(load().pc_occupancy_fixed(W, L, int(n_metallic), int(seed) & (2**64 - 1), config_begin,
+                                     n_configs, _ptr(out), _stream_handle(stream)))
+    return out
+
+
 def _alloc_outputs(n: int, device: bool, want: tuple):
     if device:
         import torch
@@ -171,8 +187,11 @@ ALL_OUTPUTS = ("first_hit", "mass", "m_stop")
 
 def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs: int, *,
                device: bool = False, want: tuple = ALL_OUTPUTS, mode: int = 0,
-               stream=None, out: dict | None = None) -> dict:
+               stream=None, out: dict | None = None, bits_only: bool = False) -> dict:
     """Inspect configurations config_begin..+n_configs-1 (Sec. II.B, Eqs. (1)-(4)).
+
+    bits_only: propagate the exact reached set alone (verdicts, first_hit,
+    m_stop; mass is 0).
 
     device=False: numpy outputs plus ``n_percolating`` and ``Pi`` (the call
     synchronises).  device=True: torch CUDA tensors written asynchronously on
@@ -180,7 +199,7 @@ def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs
     ``out`` may pass preallocated outputs of the same form.
     """
     o = out if out is not None else _alloc_outputs(n_configs, device, want)
-    flags = mode | (PC_OUT_DEVICE if device else 0)
+    flags = mode | (PC_OUT_DEVICE if device else 0) | (PC_BITS_ONLY if bits_only else 0)
     npc = ctypes.c_int64(0); pi = ctypes.c_double(0.0)
     _check(load().pc_inspect(
         W, L, float(p), int(seed) & (2**64 - 1), config_begin, n_configs,
@@ -262,7 +281,7 @@ def batch_queries(specs, *, device: bool, outs: list | None = None):
 
 
 def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=None,
-                 outs: list | None = None, queries=None):
+                 outs: list | None = None, queries=None, bits_only: bool = False):
     """Inspect a batch of queries [(W, L, p, seed, config_begin, n_configs)] in
     one submission (one cached CUDA graph).  Returns (outs, results): per-query
     outputs (numpy, or torch CUDA tensors with ``device``) and the host
@@ -270,7 +289,7 @@ def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=No
     ``queries``) again replays the cached graph."""
     if queries is None:
         queries, outs = batch_queries(specs, device=device, outs=outs)
-    flags = (PC_OUT_DEVICE if device else 0) | (PC_ASYNC if async_ else 0)
+    flags = (PC_OUT_DEVICE if device else 0) | (PC_ASYNC if async_ else 0) | (PC_BITS_ONLY if bits_only else 0)
     res = None if async_ else (PcResult * len(specs))()
     _check(load().pc_batch_run(ctypes.addressof(queries), len(specs),
                                None if res is None else ctypes.addressof(res), flags,

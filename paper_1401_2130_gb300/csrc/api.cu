@@ -147,6 +147,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       a.n_cfg = n; a.cfg0 = (uint32_t)cfg0;
       a.verdict = s.verdict; a.first_hit = s.first_hit; a.mass = s.mass; a.m_stop = s.m_stop;
       a.n_perc = s.n_perc; a.work = s.work; a.prep_chunk = 8;
+      a.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
       rc = launch_resident(a, tuned_threads(lat, occ_bits ? 0.2 : p, seed, st), st);
     } else {
       StreamJob j;
@@ -154,6 +155,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       j.n_cfg = n; j.cfg0 = (uint32_t)cfg0;
       j.out.verdict = s.verdict; j.out.first_hit = s.first_hit; j.out.mass = s.mass;
       j.out.m_stop = s.m_stop; j.out.n_perc = s.n_perc;
+      j.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
       j.error_out = (int*)(s.work + 2);
       rc = run_stream(j, st);
     }
@@ -218,6 +220,28 @@ pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed, int64_t co
   os.T = threshold_of(p);
   return launch_occupancy(lat, os, (uint32_t)config_begin, n_configs, occ_bits,
                           (cudaStream_t)cuda_stream);
+}
+
+pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t seed,
+                             int64_t config_begin, int64_t n_configs, uint32_t* occ_bits,
+                             void* cuda_stream) {
+  pc_status rc = check_lattice(W, L);
+  if (rc) return rc;
+  const int64_t N = n_columns(W) * (int64_t)L;
+  if (n_metallic < 0 || n_metallic > N) { set_error("n_metallic must be in [0, N]"); return PC_ERR_ARG; }
+  if ((rc = check_range(config_begin, n_configs))) return rc;
+  if (n_configs == 0) return PC_OK;
+  if (!occ_bits) { set_error("occ_bits must not be NULL"); return PC_ERR_ARG; }
+  Lattice lat;
+  if ((rc = get_lattice(W, L, &lat))) return rc;
+  OccStream os;
+  os.k0 = (uint32_t)(seed & 0xffffffffu);
+  os.k1 = (uint32_t)(seed >> 32);
+  os.cfg = 0;
+  os.wl = (uint32_t)W | ((uint32_t)L << 8);
+  os.T = 0;
+  return launch_occupancy_fixed(lat, os, (uint32_t)config_begin, n_configs, n_metallic, occ_bits,
+                                (cudaStream_t)cuda_stream);
 }
 
 pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed, int64_t config_begin,

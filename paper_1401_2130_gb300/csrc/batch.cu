@@ -227,6 +227,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         a.n_cfg = q[i].n_configs; a.cfg0 = (uint32_t)q[i].config_begin;
         a.verdict = P.v; a.first_hit = P.fh; a.mass = P.mass; a.m_stop = P.ms;
         a.n_perc = P.n_perc; a.work = ctr + 2 * i + 1; a.prep_chunk = 8;
+        a.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
         if (!a.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
         cudaGraphNode_t node;
         rc = resident_add_node(a, P.threads, b->graph, &n_zero, 1, &node);
@@ -237,6 +238,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         s.n_cfg = q[i].n_configs; s.cfg0 = (uint32_t)q[i].config_begin;
         s.out.verdict = P.v; s.out.first_hit = P.fh; s.out.mass = P.mass; s.out.m_stop = P.ms;
         s.out.n_perc = P.n_perc;
+        s.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
         if (!s.out.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
         sq.push_back(s);
       }

@@ -29,6 +29,7 @@ struct ResidentArgs {
   unsigned long long* n_perc;
   unsigned long long* work;  // zeroed work counter
   int prep_chunk;            // layers prepared per lazy chunk (>= 3)
+  int bits_only = 0;         // reached set only: no FP32 sweep, mass written 0
 };
 size_t resident_smem(const Lattice& lat);
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st);
@@ -51,6 +52,7 @@ struct StreamQuery {
   int64_t n_cfg;
   uint32_t cfg0;
   Outputs out;
+  int bits_only = 0;  // reached set only: no FP units, mass written 0
 };
 struct StreamJob : StreamQuery {
   int* error_out = nullptr;  // device int: 1 if the tick bound was hit
@@ -76,11 +78,19 @@ pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& q,
 pc_status server_engine_bind(ServerEngine* E, const int* slots, const int* queries, char* const* bases,
                              int n, cudaStream_t st);
 pc_status server_engine_run_chunk(ServerEngine* E, cudaStream_t st);
-pc_status server_engine_status(ServerEngine* E, cudaStream_t st, const int** phases,
+// Enqueue a status read into host buffer buf (0 or 1): slot phases and
+// per-query completion counts; the buffers are valid once the stream passes.
+pc_status server_engine_status(ServerEngine* E, cudaStream_t st, int buf, const int** phases,
                                const unsigned long long** qdone);
+const int* server_engine_phase_buffer(const ServerEngine* E, int buf);
+const unsigned long long* server_engine_qdone_buffer(const ServerEngine* E, int buf);
 
 // Standalone occupancy draw, occupancy.cu.
 pc_status launch_occupancy(const Lattice& lat, const OccStream& os, uint32_t cfg0,
                            int64_t n_cfg, uint32_t* occ_bits, cudaStream_t st);
+// Fixed-count occupancy (exactly n_metallic sites per configuration); waits
+// for its own work on st (a convergence check).
+pc_status launch_occupancy_fixed(const Lattice& lat, const OccStream& os, uint32_t cfg0, int64_t n_cfg,
+                                 int64_t n_metallic, uint32_t* occ_bits, cudaStream_t st);
 
 }  // namespace pc

@@ -160,7 +160,8 @@ __device__ inline uint32_t shifted_word(const uint32_t* R, int S, int col, int t
 // the degrees of layer Fnew - 1), degrees (Eq. (2), detector edge on t = L-1),
 // nu planes zeroed in both buffers.  Block-uniform.
 __device__ __forceinline__ void prepare_layers(const Smem& sm, const Lattice& lat, const OccStream& os,
-                                               const uint32_t* cbits, int& G, int& F, int Fnew) {
+                                               const uint32_t* cbits, int& G, int& F, int Fnew,
+                                               bool bits_only) {
   const int tid = threadIdx.x, T = blockDim.x;
   const int A = lat.A, L = lat.L, S = lat.S, P = lat.P;
   const int Gnew = min(Fnew + 1, L);
@@ -197,7 +198,7 @@ __device__ __forceinline__ void prepare_layers(const Smem& sm, const Lattice& la
     G = Gnew;
     __syncthreads();
   }
-  const int n = (Fnew - F) * P;
+  const int n = bits_only ? 0 : (Fnew - F) * P;  // degrees and nu: FP sweep only
   for (int k = tid; k < n; k += T) {
     const int t = F + k / P, pos = k % P;
     const int a = __ldg(lat.pcol + pos);
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
   __syncthreads();
 
   const int CH = Pa.prep_chunk;
+  const bool bits_only = Pa.bits_only != 0;
   const int n_words_col = S * TWP;
   // when the CTA has a thread per column, that thread owns the column's
   // reached-set words and keeps its neighbour table (packed int16 pairs)
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
     os.cfg = cfg;
     const uint32_t* cbits = Pa.occ_bits ? Pa.occ_bits + (size_t)rel * Pa.words_per_cfg : nullptr;
 
-    prepare_layers(sm, lat, os, cbits, G, F, min(max(CH, 3), L));
+    prepare_layers(sm, lat, os, cbits, G, F, min(max(CH, 3), L), bits_only);
 
     // ---- m = 0: start distribution on the metallic sites of t = 0 ----
     long long my_n0 = 0;
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
     float mass = 0.f;
     if (n0 > 0) {
       const float inv_n0 = __frcp_rn((float)n0);
-      for (int a = tid; a < A; a += T) {
+      for (int a = bits_only ? A : tid; a < A; a += T) {
         const int pos = __ldg(lat.ppos + a);
         sm.nu[0][2 * P + pos] = (sm.occw[S + a] & 1u) ? sm.inv[sm.dg[pos]] * inv_n0 : 0.f;
       }
@@ -296,12 +298,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
       if (L == 1) {
         float part = 0.f;
         for (int k = tid; k < P; k += T) part += sm.nu[0][2 * P + k];
-        mass = block_sum_f(part, sm.redf);
+        mass = bits_only ? 0.f : block_sum_f(part, sm.redf);
         verdict = 1; fh = 1; mstop = 1;
       } else {
         for (int m = 1;; ++m) {
           const int tmax = min(m, L - 1);
-          if (F < min(m + 3, L)) prepare_layers(sm, lat, os, cbits, G, F, min(max(F + CH, m + 3), L));
+          if (F < min(m + 3, L)) prepare_layers(sm, lat, os, cbits, G, F, min(max(F + CH, m + 3), L), bits_only);
           const bool odd = (m & 1) != 0;  // step m reads buffer (m-1)&1, writes m&1
           const float* __restrict__ src = odd ? sm.nu[0] : sm.nu[1];
           float* __restrict__ dst = odd ? sm.nu[1] : sm.nu[0];
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
           int CL = (nl + K - 1) / K;
           CL = CL < 2 ? 2 : CL;
           const int nch = (nl + CL - 1) / CL;
-          for (int it = tid; it < NS * nch; it += T) {
+          for (int it = bits_only ? NS * nch : tid; it < NS * nch; it += T) {
             const int c = it / NS, k = it - c * NS;
             const int t0 = c * CL, t1 = min(t0 + CL, nl);
             const int* ro = sm.roff + 4 * sm.srow[k];
@@ -359,8 +361,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
           if (tid == 0) sm.flags[(m + 2) % 3] = 0u;
           if (f & kEnd) {
             float part = 0.f;
-            for (int k = tid; k < P; k += T) part += dst[(size_t)(L + 1) * P + k];
-            mass = block_sum_f(part, sm.redf);
+            for (int k = bits_only ? P : tid; k < P; k += T) part += dst[(size_t)(L + 1) * P + k];
+            mass = bits_only ? 0.f : block_sum_f(part, sm.redf);
             verdict = 1; fh = m + 1; mstop = m + 1;
             break;
           }

@@ -87,6 +87,7 @@ struct Ticket {
   size_t off_out = 0, bytes_out = 0, off_slots = 0, bytes_slots = 0;
   int nslots = 0;
   std::vector<int> slot_ids;    // slots reserved at admission (streamed)
+  uint64_t start_seq = 0;       // first tick chunk enqueued after the query's binding
   cudaEvent_t ev = nullptr;
   unsigned long long* n_perc = nullptr;
   uint8_t* v = nullptr; int32_t* fh = nullptr; float* mass = nullptr; int32_t* ms = nullptr;
@@ -99,6 +100,7 @@ struct pc_server {
   pc_server_opts opts;
   int device = 0;
   cudaStream_t tick = nullptr;
+  cudaStream_t copy = nullptr;  // output copies of finished streamed queries
   cudaStream_t res[pc::kResStreams] = {};
   int res_rr = 0;
   pc::ServerEngine* E = nullptr;
@@ -215,6 +217,10 @@ void finish_query(pc_server* s, uint64_t id, Ticket& t, cudaStream_t st) {
 void worker_main(pc_server* s) {
   cudaSetDevice(s->device);
   std::vector<uint64_t> running;
+  cudaEvent_t ev[2] = {};
+  for (int b = 0; b < 2; ++b) cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming);
+  uint64_t next_seq = 0;  // sequence number of the next tick chunk
+  int inflight = 0;       // chunks enqueued whose status has not been read
   for (;;) {
     // ---- admission (arrival order; stops at the first query that does not fit)
     std::vector<uint64_t> to_start;
@@ -283,21 +289,42 @@ void worker_main(pc_server* s) {
         if (tp->qi >= 0) s->query_owner[tp->qi] = 0;
         s->cv_done.notify_all();
       } else {
+        tp->start_seq = next_seq;
         running.push_back(id);
       }
     }
-    // ---- device work
+    // ---- device work: keep two tick chunks in flight while streamed queries
+    // run, so the host's bookkeeping for chunk c overlaps chunk c + 1 on the
+    // device.  Work enqueued now (bindings) lands after the chunks in flight:
+    // a status is trusted only for queries bound before its chunk.
     bool streamed = false;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       for (uint64_t id : running) if (s->tickets[id].kind == 1) streamed = true;
     }
+    while (streamed && inflight < 2) {
+      const int b = (int)(next_seq & 1);
+      const int* ph = nullptr;
+      const unsigned long long* qd = nullptr;
+      if (server_engine_run_chunk(s->E, s->tick) || server_engine_status(s->E, s->tick, b, &ph, &qd) ||
+          cudaEventRecord(ev[b], s->tick) != cudaSuccess) {
+        break;
+      }
+      ++next_seq;
+      ++inflight;
+    }
     const int* phases = nullptr;
     const unsigned long long* qdone = nullptr;
-    if (streamed) {
-      server_engine_run_chunk(s->E, s->tick);
-      server_engine_status(s->E, s->tick, &phases, &qdone);
-      cudaStreamSynchronize(s->tick);
+    uint64_t seen = 0;  // chunk whose status is read this iteration
+    bool have_status = false;
+    if (inflight > 0) {
+      seen = next_seq - (uint64_t)inflight;
+      const int b = (int)(seen & 1);
+      cudaEventSynchronize(ev[b]);
+      phases = s->E ? server_engine_phase_buffer(s->E, b) : nullptr;
+      qdone = s->E ? server_engine_qdone_buffer(s->E, b) : nullptr;
+      have_status = true;
+      --inflight;
     }
     // ---- completions
     std::vector<uint64_t> still;
@@ -309,29 +336,35 @@ void worker_main(pc_server* s) {
       }
       bool done = false;
       if (tp->kind == 0) done = cudaEventQuery(tp->ev) == cudaSuccess;
-      else done = qdone && qdone[tp->qi] >= (unsigned long long)tp->q.n_configs;
-      if (done) finish_query(s, id, *tp, tp->kind == 0 ? s->res[tp->stream_idx] : s->tick);
+      else done = have_status && tp->start_seq <= seen && qdone[tp->qi] >= (unsigned long long)tp->q.n_configs;
+      if (done) finish_query(s, id, *tp, tp->kind == 0 ? s->res[tp->stream_idx] : s->copy);
       else still.push_back(id);
     }
     // free slots of queries that have handed back (phase EMPTY) but run on
-    if (phases) {
+    if (have_status) {
       std::lock_guard<std::mutex> lk(s->mu);
-      for (size_t i = 0; i < s->slot_owner.size(); ++i)
-        if (s->slot_owner[i] && phases[i] == 0) {
-          // keep the slot reserved until its query finishes: its memory is
-          // the query's; only the slot index is released for rebinding
-          s->slot_owner[i] = 0;
-        }
+      for (size_t i = 0; i < s->slot_owner.size(); ++i) {
+        const uint64_t o = s->slot_owner[i];
+        if (!o || phases[i] != 0) continue;
+        auto it = s->tickets.find(o);
+        // a slot bound after the chunk was enqueued still reads EMPTY there
+        if (it != s->tickets.end() && it->second.start_seq > seen) continue;
+        // keep the slot's memory with its query until the query finishes;
+        // only the slot index is released for rebinding
+        s->slot_owner[i] = 0;
+      }
     }
     running.swap(still);
-    if (running.empty()) {
+    if (running.empty() && inflight == 0) {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
       if (s->pending.empty()) s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-    } else if (!streamed) {
+    } else if (!streamed && inflight == 0) {
       std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
   }
+  cudaStreamSynchronize(s->tick);
+  for (int b = 0; b < 2; ++b) cudaEventDestroy(ev[b]);
 }
 
 }  // namespace
@@ -361,12 +394,14 @@ pc_status pc_server_create(const pc_server_opts* opts, pc_server** out) {
   s->opts = o;
   cudaGetDevice(&s->device);
   cudaError_t e = cudaStreamCreateWithFlags(&s->tick, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
   for (int i = 0; i < kResStreams && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&s->res[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->arena_mem, o.hbm_budget_bytes);
   if (e != cudaSuccess) {
     pc_status rc = cuda_fail(e, "pc_server_create");
     if (s->arena_mem) cudaFree(s->arena_mem);
     if (s->tick) cudaStreamDestroy(s->tick);
+    if (s->copy) cudaStreamDestroy(s->copy);
     for (auto r : s->res) if (r) cudaStreamDestroy(r);
     delete s;
     return rc == PC_ERR_CUDA && e == cudaErrorMemoryAllocation ? PC_ERR_OOM : rc;
@@ -377,6 +412,7 @@ pc_status pc_server_create(const pc_server_opts* opts, pc_server** out) {
   if (rc) {
     cudaFree(s->arena_mem);
     cudaStreamDestroy(s->tick);
+    cudaStreamDestroy(s->copy);
     for (auto r : s->res) cudaStreamDestroy(r);
     delete s;
     return rc;
@@ -497,6 +533,7 @@ pc_status pc_server_destroy(pc_server* s) {
   server_engine_destroy(s->E);
   cudaFree(s->arena_mem);
   cudaStreamDestroy(s->tick);
+  cudaStreamDestroy(s->copy);
   for (auto r : s->res) cudaStreamDestroy(r);
   delete s;
   return PC_OK;

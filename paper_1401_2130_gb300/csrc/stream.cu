@@ -47,7 +47,7 @@ enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS 
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
 constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
 constexpr int kRowsFP = 64;   // layers per FP unit (the ring prologue is paid once per unit)
-constexpr int kMaxRing = 16;  // ring slots: planes in flight ahead of the compute
+constexpr int kMaxRing = 8;  // ring slots: planes in flight ahead of the compute (deeper rings cost L1)
 // shared memory the ring may take per CTA (two sweep CTAs per SM)
 constexpr int kRingBudget = 104 * 1024;
 constexpr int kMaxSlots = 4096;
@@ -72,6 +72,7 @@ struct QDev {
   uint32_t cfg0;
   Outputs out;
   long long item0;  // first global work item of this query
+  int bits_only;    // reached set only: no FP units, mass written 0
 };
 
 struct __align__(16) Ctl {
@@ -193,13 +194,6 @@ __device__ inline uint32_t bit_at(const uint32_t* w, int S, int col, int tt) {
   return (w[((tt >> 5) + 1) * S + col] >> (tt & 31)) & 1u;
 }
 
-__device__ inline uint32_t shifted_word(const uint32_t* R, int S, int col, int tw, int dt) {
-  const uint32_t w = R[(tw + 1) * S + col];
-  if (dt == 0) return w;
-  if (dt > 0) return (w >> 1) | (R[(tw + 2) * S + col] << 31);
-  return (w << 1) | (R[tw * S + col] >> 31);
-}
-
 // query of a global work item (queries are few; linear scan)
 __device__ inline int query_of(const Ctx& x, long long item) {
   int q = 0;
@@ -207,9 +201,10 @@ __device__ inline int query_of(const Ctx& x, long long item) {
   return q;
 }
 
-__device__ inline void fill_plan(Ctl& c, const Lattice& lat) {
-  const Plan p = make_plan(c.phase, c.m, c.G, c.F, lat.L, lat.TW);
-  for (int k = 0; k < U_KINDS; ++k) c.units[k] = units_of(k, p.lo[k], p.hi[k], lat);
+__device__ inline void fill_plan(Ctl& c, const QDev& Q) {
+  const Plan p = make_plan(c.phase, c.m, c.G, c.F, Q.lat.L, Q.lat.TW);
+  for (int k = 0; k < U_KINDS; ++k) c.units[k] = units_of(k, p.lo[k], p.hi[k], Q.lat);
+  if (Q.bits_only) c.units[U_FP] = 0;
 }
 
 __device__ inline void assign(const Ctx& x, Ctl& c, unsigned long long item) {
@@ -218,7 +213,7 @@ __device__ inline void assign(const Ctx& x, Ctl& c, unsigned long long item) {
   if ((long long)item < x.n_items) {
     c.q = query_of(x, (long long)item);
     c.phase = PH_DRAW0;
-    fill_plan(c, x.qs[c.q].lat);
+    fill_plan(c, x.qs[c.q]);
   } else {
     c.q = 0; c.phase = PH_EMPTY;
   }
@@ -313,9 +308,10 @@ struct Ring {
 // three planes below it, are copied into the next ring slot by thread 0
 // (cp.async.bulk; an mbarrier per slot counts the bytes).  Planes take ring
 // slots in the order they are copied, continuing across units: plane t0+1 of
-// this unit is in slot rg.base.  After each layer a block barrier frees the
-// slot of plane t+2 and thread 0 refills it with plane t+2+nring, so the
-// copies run nring-1 layers ahead of their use.  A wait that expires sets
+// this unit is in slot rg.base.  After each pair of layers a block barrier
+// frees the slots of the two planes the pair is done with and thread 0
+// refills them nring planes further on, so the copies run at least nring-3
+// layers ahead of their use.  A wait that expires sets
 // error bit 2 and *abort; the thread then skips all further waits and
 // copies, and the kernel drains the copies in flight and returns after the
 // unit.
@@ -399,6 +395,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   }
   __syncthreads();  // plane t0 + 1's slot is free
   issue(t0 + 1 + nring, s1);
+  // layers in pairs: one block barrier frees the two planes the pair is done with
   int t = t0;
   for (;;) {
     wait(s3);
@@ -411,10 +408,13 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
     }
-    __syncthreads();  // plane t + 2's slot is free
-    issue(t + 2 + nring, s2);
+    const int fa = s2;  // plane t + 2: done
     s2 = s3; s3 = inc(s3);
-    if (++t >= t1) break;
+    if (++t >= t1) {
+      __syncthreads();
+      issue(t + 1 + nring, fa);
+      break;
+    }
     wait(s3);
     if (have) {
       load_runs(A, ring + (size_t)s3 * cap, u0, d0, c0);
@@ -425,9 +425,11 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
     }
-    __syncthreads();
-    issue(t + 2 + nring, s2);
+    const int fb = s2;  // plane t + 2: done
     s2 = s3; s3 = inc(s3);
+    __syncthreads();    // planes t + 1 and t + 2 are free
+    issue(t + 1 + nring, fa);
+    issue(t + 2 + nring, fb);
     if (++t >= t1) break;
   }
   // s2 now holds plane t1 + 2 (the last); the next unit continues after it
@@ -552,14 +554,16 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
         }
         for (int t = t0; t < t1; ++t) {
           int deg = 0;
-          if (col >= 0 && bit_at(v.occw, S, col, t)) {
+          if (col >= 0 && !Q.bits_only && bit_at(v.occw, S, col, t)) {
             deg = (int)bit_at(v.occw, S, col, t - 1) + (int)bit_at(v.occw, S, col, t + 1) + (t == L - 1);
 #pragma unroll
             for (int d = 0; d < kLateral; ++d) deg += (int)bit_at(v.occw, S, nb[d], t + dir_dt(d, sg));
           }
-          v.dg[(size_t)t * P + pos] = (uint8_t)deg;
-          v.nu0[(size_t)(t + 2) * P + pos] = 0.f;
-          v.nu1[(size_t)(t + 2) * P + pos] = 0.f;
+          if (!Q.bits_only) {
+            v.dg[(size_t)t * P + pos] = (uint8_t)deg;
+            v.nu0[(size_t)(t + 2) * P + pos] = 0.f;
+            v.nu1[(size_t)(t + 2) * P + pos] = 0.f;
+          }
           if (col >= 0 && (t & 31) == 0) {  // reached-set word rows cleaned one row ahead
             const int wr = (t >> 5) + 2;
             v.R0[wr * S + col] = 0u; v.R1[wr * S + col] = 0u;
@@ -685,6 +689,7 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
         for (int a = tid; a < A; a += blockDim.x) {
           const uint32_t b = v.occw[S + a] & 1u;
           v.R0[S + a] = b;
+          if (Q.bits_only) continue;
           const int pos = __ldg(lat.ppos + a);
           const int d = v.dg[pos];
           const float val = b ? (d ? __frcp_rn((float)d) : 0.f) * inv : 0.f;
@@ -692,7 +697,7 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
           part += val;
         }
         if (L == 1) {
-          mass = block_sum_f(part, red);
+          mass = Q.bits_only ? 0.f : block_sum_f(part, red);
           finish = true; verdict = 1; fh = 1; mstop = 1;
         } else {
           c.phase = PH_STEP; c.m = 1; c.flags = 0u;
@@ -705,8 +710,9 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
       if (f & kEnd) {
         const float* dst = (c.m & 1) ? v.nu1 : v.nu0;
         float part = 0.f;
-        for (int k = tid; k < lat.P; k += blockDim.x) part += dst[(size_t)(L + 1) * lat.P + k];
-        mass = block_sum_f(part, red);
+        for (int k = Q.bits_only ? lat.P : tid; k < lat.P; k += blockDim.x)
+          part += dst[(size_t)(L + 1) * lat.P + k];
+        mass = Q.bits_only ? 0.f : block_sum_f(part, red);
         finish = true; verdict = 1; fh = c.m + 1; mstop = c.m + 1;
       } else if (!(f & kGrow)) {
         finish = true; mstop = c.m;
@@ -730,13 +736,13 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
           const int q = c.q;
           c.item = (long long)nxt; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
           for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
-          if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q].lat); }
+          if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q]); }
           else c.phase = PH_EMPTY;
         } else {
           assign(x, c, atomicAdd(x.work, 1ull));
         }
       } else {
-        fill_plan(c, lat);
+        fill_plan(c, Q);
       }
       x.ctl[slot] = c;
     }
@@ -787,7 +793,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   for (int i = 0; i < nq; ++i) {
     h[i].lat = qs[i].lat; h[i].occ = qs[i].occ; h[i].occ_bits = qs[i].occ_bits;
     h[i].words_per_cfg = qs[i].words_per_cfg; h[i].n_cfg = qs[i].n_cfg; h[i].cfg0 = qs[i].cfg0;
-    h[i].out = qs[i].out; h[i].item0 = n_items;
+    h[i].out = qs[i].out; h[i].item0 = n_items; h[i].bits_only = qs[i].bits_only;
     n_items += qs[i].n_cfg;
     slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L, qs[i].lat.P));
     max_steps = std::max<unsigned long long>(max_steps, (unsigned long long)qs[i].lat.N + 4);
@@ -923,7 +929,7 @@ __global__ void __launch_bounds__(1024) server_bind_kernel(Ctx x, BindList b) {
     const unsigned long long nxt = atomicAdd(&x.qnext[q], 1ull);
     c.item = (long long)nxt; c.q = q; c.m = 0; c.G = 0; c.F = 0; c.flags = 0u;
     for (int k = 0; k < U_KINDS; ++k) c.units[k] = 0;
-    if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q].lat); }
+    if ((long long)nxt < x.qs[q].n_cfg) { c.phase = PH_DRAW0; fill_plan(c, x.qs[q]); }
     else c.phase = PH_EMPTY;
     x.ctl[s] = c;
   }
@@ -953,8 +959,8 @@ struct ServerEngine {
   Ctx x;
   char* mem = nullptr;
   int* d_phase = nullptr;
-  int* h_phase = nullptr;                 // pinned [K]
-  unsigned long long* h_qdone = nullptr;  // pinned [nq]
+  int* h_phase[2] = {};                 // pinned [K], one per status buffer
+  unsigned long long* h_qdone[2] = {};  // pinned [nq]
   cudaGraphExec_t chunk = nullptr;
   int max_queries = 0;
 };
@@ -997,8 +1003,11 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     if ((e = cudaMemsetAsync(E->mem, 0, bytes, st)) != cudaSuccess) { rc = cuda_fail(e, "server memset"); break; }
     server_reset_kernel<<<1, 1024, 0, st>>>(x);
     if ((e = cudaGetLastError()) != cudaSuccess) { rc = cuda_fail(e, "server reset"); break; }
-    if ((e = cudaMallocHost((void**)&E->h_phase, sizeof(int) * K)) != cudaSuccess) { rc = cuda_fail(e, "pinned"); break; }
-    if ((e = cudaMallocHost((void**)&E->h_qdone, sizeof(unsigned long long) * nq)) != cudaSuccess) { rc = cuda_fail(e, "pinned"); break; }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaMallocHost((void**)&E->h_phase[b], sizeof(int) * K);
+      if (e == cudaSuccess) e = cudaMallocHost((void**)&E->h_qdone[b], sizeof(unsigned long long) * nq);
+    }
+    if (e != cudaSuccess) { rc = cuda_fail(e, "pinned"); break; }
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1035,8 +1044,10 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
 void server_engine_destroy(ServerEngine* E) {
   if (!E) return;
   if (E->chunk) cudaGraphExecDestroy(E->chunk);
-  if (E->h_phase) cudaFreeHost(E->h_phase);
-  if (E->h_qdone) cudaFreeHost(E->h_qdone);
+  for (int b = 0; b < 2; ++b) {
+    if (E->h_phase[b]) cudaFreeHost(E->h_phase[b]);
+    if (E->h_qdone[b]) cudaFreeHost(E->h_qdone[b]);
+  }
   if (E->mem) cudaFree(E->mem);
   delete E;
 }
@@ -1049,7 +1060,7 @@ pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& sq
   ch.base = qi; ch.n = 1;
   QDev& d = ch.q[0];
   d.lat = sq.lat; d.occ = sq.occ; d.occ_bits = sq.occ_bits; d.words_per_cfg = sq.words_per_cfg;
-  d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0;
+  d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0; d.bits_only = sq.bits_only;
   upload_queries_kernel<<<1, kQChunk, 0, st>>>((QDev*)E->x.qs, ch);
   PC_CUDA(cudaGetLastError());
   PC_CUDA(cudaMemsetAsync(E->x.qnext + qi, 0, sizeof(unsigned long long), st));
@@ -1076,15 +1087,18 @@ pc_status server_engine_run_chunk(ServerEngine* E, cudaStream_t st) {
 
 // Enqueue the copy of slot phases and per-query completion counts to pinned
 // host memory; valid after st reaches this point.
-pc_status server_engine_status(ServerEngine* E, cudaStream_t st, const int** phases,
+const int* server_engine_phase_buffer(const ServerEngine* E, int buf) { return E->h_phase[buf]; }
+const unsigned long long* server_engine_qdone_buffer(const ServerEngine* E, int buf) { return E->h_qdone[buf]; }
+
+pc_status server_engine_status(ServerEngine* E, cudaStream_t st, int buf, const int** phases,
                                const unsigned long long** qdone) {
   server_status_kernel<<<1, 1024, 0, st>>>(E->x, E->d_phase);
   PC_CUDA(cudaGetLastError());
-  PC_CUDA(cudaMemcpyAsync(E->h_phase, E->d_phase, sizeof(int) * E->x.K, cudaMemcpyDeviceToHost, st));
-  PC_CUDA(cudaMemcpyAsync(E->h_qdone, E->x.qdone, sizeof(unsigned long long) * E->max_queries,
+  PC_CUDA(cudaMemcpyAsync(E->h_phase[buf], E->d_phase, sizeof(int) * E->x.K, cudaMemcpyDeviceToHost, st));
+  PC_CUDA(cudaMemcpyAsync(E->h_qdone[buf], E->x.qdone, sizeof(unsigned long long) * E->max_queries,
                           cudaMemcpyDeviceToHost, st));
-  *phases = E->h_phase;
-  *qdone = E->h_qdone;
+  *phases = E->h_phase[buf];
+  *qdone = E->h_qdone[buf];
   return PC_OK;
 }
 

@@ -158,10 +158,11 @@ COARSE_P = tuple(round(0.08 + 0.02 * i, 2) for i in range(27))  # 0.08 .. 0.60
 
 def measure(specs):
     """Percolating counts of queries [(W, L, p, seed, config_begin, n)], all
-    in one batched GPU submission (pc_batch_run)."""
+    in one batched GPU submission (pc_batch_run).  Only verdicts are needed,
+    so the batch propagates the exact reached set alone (PC_BITS_ONLY)."""
     from . import pc_batch_run
 
-    _, res = pc_batch_run(list(specs), device=False)
+    _, res = pc_batch_run(list(specs), device=False, bits_only=True)
     return [r["n_percolating"] for r in res]
 
 
@@ -210,3 +211,49 @@ def extrapolate(curves, nu: float = NU_3D):
         except RuntimeError:
             law = None
     return f, law
+
+
+# ---------------------------------------------------------------------------
+# Length dependence at fixed width (Sec. III, Fig. 6(a)): Pi ~ exp(-lambda L)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class DecayFit:
+    lam: float      # mean block failure rate lambda_bar: Pi ~ exp(-lambda_bar L)
+    lam_err: float
+    n_points: int   # lengths with 0 < Pi < 1 used in the fit
+
+
+def decay_rate(L, k, n) -> DecayFit:
+    """Fit ln Pi(L) = c - lambda_bar L (Sec. III: the fibre as a chain of
+    blocks, Pi = prod (1 - lambda_i) ~ exp(-lambda_bar L)) by weighted least
+    squares over the lengths with 0 < k < n; var(ln Pi) ~ (1 - Pi) / (n Pi)."""
+    L = np.asarray(L, dtype=float)
+    k = np.asarray(k, dtype=float)
+    n = np.asarray(n, dtype=float)
+    use = (k > 0) & (k < n)
+    if use.sum() < 2:
+        # fully percolating (or never) over the range: no measurable decay
+        return DecayFit(0.0 if np.all(k == n) else float("inf"), 0.0, int(use.sum()))
+    Pi = k[use] / n[use]
+    y = np.log(Pi)
+    w = n[use] * Pi / (1.0 - Pi)
+    X = np.stack([np.ones(use.sum()), -L[use]], axis=1)
+    Xw = X * np.sqrt(w)[:, None]
+    beta, *_ = np.linalg.lstsq(Xw, y * np.sqrt(w), rcond=None)
+    cov = np.linalg.pinv(Xw.T @ Xw)
+    return DecayFit(float(beta[1]), float(np.sqrt(max(cov[1, 1], 0.0))), int(use.sum()))
+
+
+def length_scan(W: int, lengths, ps, n: int, seed: int):
+    """Pi(L) at fixed W for each p (one batched submission, verdicts only).
+    Returns {p: (L array, k array, n array, DecayFit)}."""
+    lengths = [int(L) for L in lengths]
+    specs = [(W, L, float(p), seed, 0, n) for p in ps for L in lengths]
+    k = np.asarray(measure(specs), dtype=float)
+    out = {}
+    for i, p in enumerate(ps):
+        kk = k[i * len(lengths):(i + 1) * len(lengths)]
+        nn = np.full(kk.size, float(n))
+        out[float(p)] = (np.asarray(lengths), kk, nn, decay_rate(lengths, kk, nn))
+    return out

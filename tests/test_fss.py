@@ -70,3 +70,13 @@ def test_eq9_macroscopic_increment_matches_paper():
     lhs = fss.p_c_eq9(W, L, 0.15, -0.83, 0.31, -1.23)
     rhs = 0.15 + fss.slope_law(W / L, -0.83, 0.31, -1.23) * L ** (-1 / fss.NU_3D)
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_decay_rate_recovers_exponential():
+    L = np.array([4, 8, 16, 32, 64, 128, 256])
+    n = np.full(L.size, 10**8)
+    k = np.round(n * 0.97 * np.exp(-0.0123 * L))
+    f = fss.decay_rate(L, k, n)
+    assert f.lam == pytest.approx(0.0123, rel=1e-4)
+    # fully percolating over the range: no decay
+    assert fss.decay_rate(L, n, n).lam == 0.0

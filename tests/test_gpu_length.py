@@ -1,0 +1,30 @@
+"""Length dependence at fixed width (Sec. III, Fig. 6(a)) on GPU-produced
+Pi(L) curves (verdicts equal the oracle's on every configuration: the parity
+tests).  The paper states: at W = 3 and p = 0.3, Pi decays as L grows, and
+the decay is slower for higher p; at W = 6, p = 0.3 keeps the fibre
+percolating over the whole range of aspect ratios.  Seed 8, 1024
+configurations per point."""
+import numpy as np
+import pytest
+
+import paper_1401_2130_gb300 as pc
+from paper_1401_2130_gb300 import fss
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS = (4, 8, 16, 32, 64, 128, 256, 512)
+
+
+def test_w3_decays_and_slows_with_p():
+    scan = fss.length_scan(3, LENGTHS, (0.25, 0.3, 0.35, 0.4), n=1024, seed=8)
+    L, k, n, f = scan[0.3]
+    assert k[-1] < 0.5 * k[0], (k, f)  # p = 0.3, W = 3: Pi decays with L
+    lams = [scan[p][3].lam for p in (0.25, 0.3, 0.35, 0.4)]
+    assert all(a > b for a, b in zip(lams, lams[1:])), lams  # slower decay at higher p
+    assert lams[0] > 0.0
+
+
+def test_w6_p03_percolates_at_every_aspect_ratio():
+    scan = fss.length_scan(6, (6, 24, 96, 384, 1536), (0.3,), n=1024, seed=8)
+    L, k, n, f = scan[0.3]
+    assert np.all(k >= 0.97 * n), (L, k)

@@ -425,3 +425,39 @@ def test_site_update_accounting():
             assert oracle.site_updates(1, L, v, fh, ms) == brute
             if M >= 1:
                 assert oracle.site_updates(3, L, [1], [M + 1], [M + 1]) == 3 * brute
+
+
+# ---------------------------------------------------------------------------
+# fixed-count sample space (Sec. II.A: a random permutation puts exactly Np
+# of the N sites metallic)
+# ---------------------------------------------------------------------------
+
+def test_fixed_count_has_exactly_np_sites():
+    for W, L, Np in [(2, 5, 0), (2, 5, 37), (2, 5, 95), (3, 7, 100)]:
+        _, N = oracle.lattice_info(W, L)
+        occ = oracle.occupancy_fixed(W, L, min(Np, N), seed=5, cfg0=0, n=20)
+        assert np.all(occ.sum(axis=1) == min(Np, N))
+
+
+def test_fixed_count_couples_with_bernoulli():
+    # the Np sites with the smallest words are exactly the sites below the
+    # Bernoulli threshold whenever Np is the Bernoulli count
+    W, L, p, seed = 3, 9, 0.3, 17
+    bern = oracle.occupancy(W, L, p, seed, 0, 50)
+    for c in range(50):
+        Np = int(bern[c].sum())
+        fixed = oracle.occupancy_fixed(W, L, Np, seed, c, 1)[0]
+        assert np.array_equal(fixed, bern[c])
+
+
+def test_fixed_count_is_uniform_over_subsets():
+    # W = 1, L = 1: N = 7 sites, Np = 3 -> C(7, 3) = 35 subsets, equally likely
+    from math import comb
+    n = 14000
+    occ = oracle.occupancy_fixed(1, 1, 3, seed=23, cfg0=0, n=n)
+    codes = (occ.astype(np.int64) << np.arange(7)).sum(axis=1)
+    _, counts = np.unique(codes, return_counts=True)
+    assert counts.size == comb(7, 3)
+    expected = n / comb(7, 3)
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert chi2 < 70.0  # 34 degrees of freedom: P(chi2 > 70) < 1e-3
