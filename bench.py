@@ -182,6 +182,12 @@ def run_reference(args):
 # method's data: nu read 4 B + nu write 4 B + occupancy 1/8 B + reached-set
 # bit read and write 1/4 B (the per-unit figure of the measurement plan).
 HBM_BYTES_PER_SU = 8.375
+# DRAM bytes (read + write) measured with ncu on the current kernels, to be
+# re-measured whenever they change: the resident kernel per p-sweep launch
+# (tables and outputs only), and the streamed sweep per site-update
+# (controlled capture of the large lattice with 4 active slots)
+RESIDENT_DRAM_BYTES_PER_LAUNCH = 149992.0
+SWEEP_DRAM_BYTES_PER_SU = 267.04e6 / 29.95e6
 # bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
 BITS_BYTES_PER_SU = 0.375
 
@@ -243,7 +249,10 @@ def run_large(args, pc, torch):
                    "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB)"},
         "configs_per_s": n * len(ps) / t,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": None if args.bits_only else SWEEP_DRAM_BYTES_PER_SU * su,
+                     "traffic_note": "ncu DRAM bytes per site-update of sweep_kernel (controlled capture, "
+                                     "4 active slots) x the step's site-updates",
                      "model": f"{bps} B/site-update x site-updates / time of the whole "
                               "solve (sweep + control kernels), peak = measured copy bandwidth"},
         "clocks": clk.summary(),
@@ -557,7 +566,9 @@ def main():
                    "parallelism": f"configs sharded over {world} GPU(s)"},
         "configs_per_s": n_cfg * len(PS) * world / t_step,
         "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                     "frac": achieved / smem_peak, "traffic": None,
+                     "frac": achieved / smem_peak, "traffic": RESIDENT_DRAM_BYTES_PER_LAUNCH,
+                     "traffic_note": "HBM bytes per resident_kernel launch (ncu): the state lives in "
+                                     "shared memory, HBM carries tables and outputs only",
                      "model": f"{SMEM_BYTES_PER_SU} B of shared-memory traffic per site update; "
                               f"peak = {nsm} SMs x 128 B/clk x {sm_max:.0f} MHz (derived)"},
         "clocks": clocks,
