@@ -570,7 +570,12 @@ def main():
                      "traffic_note": "HBM bytes per resident_kernel launch (ncu): the state lives in "
                                      "shared memory, HBM carries tables and outputs only",
                      "model": f"{SMEM_BYTES_PER_SU} B of shared-memory traffic per site update; "
-                              f"peak = {nsm} SMs x 128 B/clk x {sm_max:.0f} MHz (derived)"},
+                              f"peak = {nsm} SMs x 128 B/clk x {sm_max:.0f} MHz (derived)",
+                     # the same throughput under the state-traffic model of
+                     # the streamed solver (8.375 B per site-update)
+                     "state_model": {"bytes_per_su": HBM_BYTES_PER_SU,
+                                     "achieved": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU,
+                                     "frac": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU / smem_peak}},
         "clocks": clocks,
         "e2e": {"value": su_step * world / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h},

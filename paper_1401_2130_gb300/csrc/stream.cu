@@ -320,14 +320,14 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
                                                uint64_t* full, Ring& rg, int* abort, const float* inv,
                                                int* s_red) {
   const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap, nring = x.nring;
-  const int k = k0 + tid;
-  const bool have = k < lat.n_strips;
-  int b = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-  int lo = 0x7fffffff, hi = -0x7fffffff;
-  if (have) {
-    b = 3 * (lat.s_begin + k);
-    const int32_t* ro = lat.row_off + 4 * lat.strip_row[k];
-    r0 = __ldg(ro); r1 = __ldg(ro + 1); r2 = __ldg(ro + 2); r3 = __ldg(ro + 3);
+  // threads past the last strip repeat it: they write the same values to
+  // the same addresses, and the layer loop needs no per-thread branch
+  const int k = min(k0 + tid, lat.n_strips - 1);
+  int lo, hi;
+  const int b = 3 * (lat.s_begin + k);
+  const int32_t* ro = lat.row_off + 4 * lat.strip_row[k];
+  const int r0 = __ldg(ro), r1 = __ldg(ro + 1), r2 = __ldg(ro + 2), r3 = __ldg(ro + 3);
+  {
     const int32_t rr[4] = {r0, r1, r2, r3};
     strip_span(b, rr, &lo, &hi);
   }
@@ -384,9 +384,9 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   int s3 = inc(s2);        // plane t + 3
   wait(s1);
   wait(s2);
-  float up2 = 0.f, dp2 = 0.f, cp[4] = {0.f, 0.f, 0.f, 0.f};
+  float up2, dp2, cp[4];
   Runs A, B;
-  if (have) {
+  {
     const float* pl = ring + (size_t)s1 * cap;
     up2 = pl[u0 + 2]; dp2 = pl[d0 + 2];
 #pragma unroll
@@ -399,7 +399,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   int t = t0;
   for (;;) {
     wait(s3);
-    if (have) {
+    {
       load_runs(B, ring + (size_t)s3 * cap, u0, d0, c0);
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
       strip_emit_deg(A, B, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
@@ -416,7 +416,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
       break;
     }
     wait(s3);
-    if (have) {
+    {
       load_runs(A, ring + (size_t)s3 * cap, u0, d0, c0);
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
       strip_emit_deg(B, A, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
@@ -1108,7 +1108,7 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st) {
   if (job.n_cfg <= 0) return PC_OK;
   StreamQuery q;
   q.lat = job.lat; q.occ = job.occ; q.occ_bits = job.occ_bits; q.words_per_cfg = job.words_per_cfg;
-  q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out;
+  q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out; q.bits_only = job.bits_only;
   StreamPlan* P = nullptr;
   pc_status rc = stream_plan_create(&q, 1, st, &P);
   if (rc) return rc;

@@ -35,17 +35,11 @@ __device__ __forceinline__ void load_runs(Runs& R, const float* __restrict__ pl,
   for (int i = 0; i < 5; ++i) R.C[i] = pl[c0 + i];
 }
 
-// Sum of 14 terms as a balanced tree (depth 4 instead of a 13-add chain).
-__device__ __forceinline__ float sum14(float a0, float a1, float a2, float a3, float a4, float a5, float a6,
-                                       float a7, float a8, float a9, float a10, float a11, float a12,
-                                       float a13) {
-  return (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) +
-         (((a8 + a9) + (a10 + a11)) + (a12 + a13));
-}
-
 // Site updates of layer t for one strip: c = runs of layer t, n = layer t+1;
 // (up2, dp2, cp) = the layer t-1 values the sublattice-0 site needs; g0..g2
-// the degrees of the three sites.
+// the degrees of the three sites.  The 14-term sums are short trees; the
+// pairs (U1 + U3, D1 + D3) and (U2 + U4, D2 + D4) are shared by neighbouring
+// sites of the strip.
 __device__ __forceinline__ void strip_emit_deg(const Runs& c, const Runs& n, float up2, float dp2,
                                                const float (&cp)[4], const float* __restrict__ plc,
                                                int e0, int f0, float* __restrict__ out_pl, int b,
@@ -53,15 +47,16 @@ __device__ __forceinline__ void strip_emit_deg(const Runs& c, const Runs& n, flo
                                                const float* __restrict__ inv) {
   const float e_0 = plc[e0], e_1 = plc[e0 + 1], e_2 = plc[e0 + 2];
   const float f_0 = plc[f0], f_1 = plc[f0 + 1], f_2 = plc[f0 + 2];
+  const float q13 = (c.U[1] + c.U[3]) + (c.D[1] + c.D[3]);  // sites 0 and 1
+  const float q24 = (c.U[2] + c.U[4]) + (c.D[2] + c.D[4]);  // sites 1 and 2
   // sublattice 0: layer-below neighbours at t-1, layer-above ones at t
-  const float s0 = sum14(c.U[3], c.U[0], c.U[1], up2, c.D[0], c.D[3], c.D[1], dp2, c.C[2], cp[0],
-                         cp[1], n.C[1], e_0, f_0);
+  const float s0 = ((q13 + (c.U[0] + up2)) + ((c.D[0] + dp2) + (c.C[2] + cp[0]))) +
+                   ((cp[1] + n.C[1]) + (e_0 + f_0));
   // sublattice 1: all in tube t (end contacts at t +- 1)
-  const float s1 = sum14(c.U[4], c.U[1], c.U[2], c.U[3], c.D[1], c.D[4], c.D[2], c.D[3], c.C[3],
-                         c.C[1], cp[2], n.C[2], e_1, f_1);
+  const float s1 = (q13 + q24) + (((c.C[3] + c.C[1]) + (cp[2] + n.C[2])) + (e_1 + f_1));
   // sublattice 2: layer-above neighbours at t+1, layer-below ones at t
-  const float s2 = sum14(c.U[5], c.U[2], n.U[3], c.U[4], c.D[2], c.D[5], n.D[3], c.D[4], n.C[4],
-                         c.C[2], cp[3], n.C[3], e_2, f_2);
+  const float s2 = ((q24 + (c.U[5] + n.U[3])) + ((c.D[5] + n.D[3]) + (n.C[4] + c.C[2]))) +
+                   ((cp[3] + n.C[3]) + (e_2 + f_2));
   out_pl[b] = inv[g0] * s0;
   out_pl[b + 1] = inv[g1] * s1;
   out_pl[b + 2] = inv[g2] * s2;

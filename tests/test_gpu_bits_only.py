@@ -43,6 +43,20 @@ def test_bits_only_equals_oracle(W, L, p, seed, cfg0, n, mode):
         assert np.array_equal(full[k], g[k]), k
 
 
+@pytest.mark.parametrize("mode", [pc.PC_MODE_RESIDENT, pc.PC_MODE_STREAM])
+def test_bits_only_skips_the_fp_recursion(mode):
+    # short fibres: the full inspection's first-passage masses are far from
+    # FP32 underflow, so a zero mass shows that the recursion did not run
+    W, L, p, seed, n = 4, 4, 0.5, 21, 256
+    full = pc.pc_inspect(W, L, p, seed, 0, n, mode=mode)
+    bits = pc.pc_inspect(W, L, p, seed, 0, n, mode=mode, bits_only=True)
+    perc = full["verdict"] != 0
+    assert perc.sum() > 50 and np.all(full["mass"][perc] > 1e-6)
+    assert not np.any(bits["mass"])
+    for k in ("verdict", "first_hit", "m_stop"):
+        assert np.array_equal(full[k], bits[k]), k
+
+
 def test_bits_only_markov_sample():
     # the Markov (FP64 CSR) oracle decides with the support of the iterate
     W, L, p, seed, n = 6, 24, 0.21, 11, 200
