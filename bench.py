@@ -186,8 +186,8 @@ HBM_BYTES_PER_SU = 8.375
 # re-measured whenever they change: the resident kernel per p-sweep launch
 # (tables and outputs only), and the streamed sweep per site-update
 # (controlled capture of the large lattice with 4 active slots)
-RESIDENT_DRAM_BYTES_PER_LAUNCH = 149992.0
-SWEEP_DRAM_BYTES_PER_SU = 267.04e6 / 29.95e6
+RESIDENT_DRAM_BYTES_PER_LAUNCH = 155160.0
+SWEEP_DRAM_BYTES_PER_SU = (266.78e6 + 269.50e6) / (29.95e6 + 30.00e6)
 # bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
 BITS_BYTES_PER_SU = 0.375
 

@@ -204,6 +204,7 @@ pc_status pc_lattice_info(int32_t W, int32_t L, int64_t* n_columns_out, int64_t*
 
 pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed, int64_t config_begin,
                        int64_t n_configs, uint32_t* occ_bits, void* cuda_stream) {
+  NvtxRange nvtx_("pc_occupancy");
   pc_status rc = check_lattice(W, L);
   if (rc) return rc;
   if (!(p >= 0.0 && p <= 1.0)) { set_error("p must be in [0, 1]"); return PC_ERR_ARG; }
@@ -225,6 +226,7 @@ pc_status pc_occupancy(int32_t W, int32_t L, double p, uint64_t seed, int64_t co
 pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t seed,
                              int64_t config_begin, int64_t n_configs, uint32_t* occ_bits,
                              void* cuda_stream) {
+  NvtxRange nvtx_("pc_occupancy_fixed");
   pc_status rc = check_lattice(W, L);
   if (rc) return rc;
   const int64_t N = n_columns(W) * (int64_t)L;
@@ -248,6 +250,7 @@ pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed, int64_t conf
                      int64_t n_configs, uint8_t* verdicts, int32_t* first_hit, float* mass,
                      int32_t* m_stop, int64_t* n_percolating, double* Pi, int32_t flags,
                      void* cuda_stream) {
+  NvtxRange nvtx_("pc_inspect");
   pc_status rc = check_lattice(W, L);
   if (rc) return rc;
   if (!(p >= 0.0 && p <= 1.0)) { set_error("p must be in [0, 1]"); return PC_ERR_ARG; }
@@ -260,6 +263,7 @@ pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits, i
                                uint8_t* verdicts, int32_t* first_hit, float* mass,
                                int32_t* m_stop, int64_t* n_percolating, double* Pi,
                                int32_t flags, void* cuda_stream) {
+  NvtxRange nvtx_("pc_inspect_occupancy");
   pc_status rc = check_lattice(W, L);
   if (rc) return rc;
   if ((rc = check_range(0, n_configs))) return rc;

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -123,6 +124,14 @@ __host__ __device__ inline void strip_span(int b, const int32_t* ro, int* lo, in
 }
 void layout_fill(int W, int* P, int* s_begin, int* n_strips, int16_t* strip_row, int32_t* row_off,
                  int32_t* ppos, int32_t* pcol);
+
+// NVTX range over a host call (profilers group the call's launches under it)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // error reporting (thread-local message), defined in api.cu
 void set_error(const std::string& msg);

@@ -121,6 +121,7 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
                                        uint8_t* verdicts, int32_t* first_hit, float* mass,
                                        int32_t* m_stop, int64_t* n_percolating, double* Pi,
                                        void* cuda_stream) {
+  NvtxRange nvtx_("pc_inspect_static");
   if (W < 0 || W > 255 || L < 1 || L >= (1 << 24)) { set_error("pc_inspect_static: bad W or L"); return PC_ERR_ARG; }
   if (!(p >= 0.0 && p <= 1.0)) { set_error("pc_inspect_static: p must be in [0, 1]"); return PC_ERR_ARG; }
   if (n_configs < 0 || config_begin < 0 || config_begin + n_configs > ((int64_t)1 << 32)) {

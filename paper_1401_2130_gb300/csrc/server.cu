@@ -233,7 +233,6 @@ void worker_main(pc_server* s) {
         if (found == s->tickets.end() || found->second.state == T_CANCELLED) { s->pending.pop_front(); continue; }
         Ticket& t = found->second;
         const pc_query& q = t.q;
-        const int64_t A = n_columns(q.W);
         const bool res = resident_fits(q.W, q.L);
         size_t off = 0;
         const size_t ob = out_bytes(q.n_configs);
