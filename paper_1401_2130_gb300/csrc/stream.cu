@@ -436,7 +436,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   rg.base = inc(s2);
 }
 
-__global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
+__global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
   // x.nring slots of x.seg_cap floats (nu planes), then x.nring of x.seg_cap bytes (degrees)
   extern __shared__ __align__(128) float ring[];
   uint8_t* dring = reinterpret_cast<uint8_t*>(ring + (size_t)x.nring * x.seg_cap);
