@@ -187,7 +187,7 @@ HBM_BYTES_PER_SU = 8.375
 # (tables and outputs only), and the streamed sweep per site-update
 # (controlled capture of the large lattice with 4 active slots)
 RESIDENT_DRAM_BYTES_PER_LAUNCH = 155160.0
-SWEEP_DRAM_BYTES_PER_SU = (266.78e6 + 269.50e6) / (29.95e6 + 30.00e6)
+SWEEP_DRAM_BYTES_PER_SU = (266.19e6 + 267.03e6) / (29.95e6 + 30.00e6)
 # bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
 BITS_BYTES_PER_SU = 0.375
 
@@ -529,7 +529,13 @@ def main():
         tt = torch.tensor([t_step], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
-    value = su_step * world / t_step
+    # the units all ranks processed (each rank inspects its own configurations)
+    su_all = su_step
+    if dist is not None:
+        st_ = torch.tensor([su_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(st_, op=dist.ReduceOp.SUM)
+        su_all = int(st_.item())
+    value = su_all / t_step
 
     # end to end through the public call with host outputs (D2H inside)
     e2e_steps = max(1, min(args.steps, 3))
@@ -560,7 +566,7 @@ def main():
                                 f"p-sweep subset W=8 L=64 p={PS[0]} seed=2"),
                    "W": W, "L": L, "n_p": len(PS), "configs_per_p": n_cfg,
                    "configs_per_step": n_cfg * len(PS) * world,
-                   "site_updates_per_step_per_gpu": su_step,
+                   "site_updates_per_step": su_all,
                    "percolating_per_p": n_perc, "solver": "resident",
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": f"configs sharded over {world} GPU(s)"},
@@ -577,7 +583,7 @@ def main():
                                      "achieved": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU,
                                      "frac": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU / smem_peak}},
         "clocks": clocks,
-        "e2e": {"value": su_step * world / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
+        "e2e": {"value": su_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": len(PS) * args.steps,
         "per_p_ms": [float(np.mean(launch_ms[i::len(PS)])) for i in range(len(PS))],

@@ -46,8 +46,8 @@ enum : int { PH_EMPTY = 0, PH_DRAW0 = 1, PH_PREP0 = 2, PH_STEP = 3 };
 enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS = 5 };
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
 constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
-constexpr int kRowsFP = 64;   // layers per FP unit (the ring prologue is paid once per unit)
-constexpr int kMaxRing = 8;  // ring slots: planes in flight ahead of the compute (deeper rings cost L1)
+constexpr int kRowsFP = 128;  // layers per FP unit (the ring prologue is paid once per unit)
+constexpr int kMaxRing = 6;  // ring slots: planes in flight ahead of the compute (deeper rings cost L1)
 // shared memory the ring may take per CTA (two sweep CTAs per SM)
 constexpr int kRingBudget = 104 * 1024;
 constexpr int kMaxSlots = 4096;
