@@ -173,9 +173,9 @@ typedef struct pc_result {
  * one pool of streamed-solver slots that refill as configurations finish; the
  * whole batch is one CUDA graph, built on the first call and replayed when
  * the same batch (same queries and output pointers) is submitted again.  The
- * resident CTA size of each (W, L) is picked by timing candidates on first
- * use (autotuner; choices kept in memory and in the JSON file named by the
- * environment variable PC_TUNE_FILE, if set).
+ * resident CTA size of each (W, L, p bin of width 0.025) is picked by timing
+ * candidates on first use (autotuner; choices kept in memory and in the JSON
+ * file named by the environment variable PC_TUNE_FILE, if set).
  * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY

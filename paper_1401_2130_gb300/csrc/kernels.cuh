@@ -37,8 +37,8 @@ pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g
                             const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out);
 // default CTA size of the resident solver (about 16 tube layers per thread)
 int resident_threads(int A, int L);
-// CTA size picked by the autotuner for (W, L) (tune.cu); times candidates on a
-// miss, outside any stream capture
+// CTA size picked by the autotuner for (W, L, p bin) (batch.cu); times
+// candidates on a miss, outside any stream capture
 int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st);
 bool resident_fits(int W, int L);
 void release_batches();

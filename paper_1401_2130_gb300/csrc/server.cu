@@ -12,9 +12,13 @@
 //     those slots to it; the engine runs chunks of ticks (sweep + control)
 //     over all bound slots of all running queries, and a slot whose query has
 //     configurations left refills itself on the device.
-// Between chunks the worker reads slot phases and per-query completion counts,
-// copies finished queries' outputs out, returns their memory and slots, and
-// admits more queries.  Latency = completion time - submission time.
+// Two chunks are kept in flight: while the device runs chunk c + 1, the
+// worker reads chunk c's slot phases and per-query completion counts, copies
+// finished queries' outputs out (on a separate stream), returns their memory
+// and slots, and admits more queries, whose bindings land after the chunks
+// already enqueued.  A status is trusted only for queries bound before its
+// chunk.  The sweep's staging ring is sized for the widest streamed lattice
+// the server accepts (max_W).  Latency = completion time - submission time.
 // Results equal pc_inspect's: the occupancy stream is counter based and the
 // per-configuration solve does not depend on what runs beside it.
 #include <algorithm>

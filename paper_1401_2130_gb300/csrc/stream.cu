@@ -13,14 +13,15 @@
 // A slot takes configurations from a global work list (all queries, largest
 // lattices first) and is refilled as soon as its configuration finishes.
 // The device runs "ticks" inside one CUDA graph conditional WHILE node:
-//   sweep   : all CTAs walk a global list of work units over all slots --
-//             FP32 site updates of step m over the causal window t <= m (a
-//             chunk of strips walks up a chunk of layers; the plane segment
-//             the chunk reads is staged into shared memory by TMA bulk copies
-//             through a 4-deep ring, three layers ahead of the compute), the
-//             exact bit-parallel reached-set update, and lazy preparation of
-//             the layers just ahead of the window (Philox draw of a word row,
-//             degrees, zeroing of nu and R rows);
+//   sweep   : a persistent grid takes work units over all slots from a
+//             per-tick counter -- FP32 site updates of step m over the causal
+//             window t <= m (a chunk of 256 strips walks up 128 layers; the
+//             plane segment and degree bytes the chunk reads are staged into
+//             shared memory by bulk copies (TMA) through a ring of up to 6
+//             slots, freed two layers at a time), the exact bit-parallel
+//             reached-set update, and lazy preparation of the layers just
+//             ahead of the window (Philox draw of a word row, degrees,
+//             zeroing of nu and R rows);
 //   control : one CTA per slot reads the step's grow / end flags, sums the
 //             detector mass on a hit (deterministic block reduction), writes
 //             the outputs, refills the slot and plans its next tick; the last
