@@ -79,7 +79,7 @@ struct Scratch {
   char* base = nullptr;
 };
 
-// Shared driver of pc_inspect / pc_inspect_occupancy.
+// Shared implementation of pc_inspect / pc_inspect_occupancy.
 pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cfg0,
                        const uint32_t* occ_bits, int64_t n, uint8_t* verdicts,
                        int32_t* first_hit, float* mass, int32_t* m_stop,
