@@ -432,6 +432,39 @@ def run_serving(args, pc, torch):
     }
 
 
+def run_fss(args, pc, torch):
+    """Finite-size scaling (Sec. III, Eqs. (5)-(9)): Pi(p) of 35 sizes,
+    W in {4, 6, 8, 12, 16, 24, 32} x W/L in {2, 1, 1/2, 1/4, 1/8}, seed 6
+    (256 configurations per p on a coarse grid, 1024 per p at 13 values
+    around each transition, verdicts only), fitted for p_c_inf and alpha."""
+    from paper_1401_2130_gb300 import fss
+    sizes = [(Wf, int(Wf / r)) for Wf in (4, 6, 8, 12, 16, 24, 32) for r in (2.0, 1.0, 0.5, 0.25, 0.125)
+             if int(Wf / r) >= 2]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    curves = fss.scan(sizes, seed=6)
+    t = time.perf_counter() - t0
+    n_cfg = len(sizes) * (len(fss.COARSE_P) * 256 + 13 * 1024)
+    fits = {}
+    for wmin in (4, 8, 12):
+        sub_ = {k: v for k, v in curves.items() if k[0] >= wmin}
+        f, law = fss.extrapolate(sub_)
+        fits[f"W>={wmin}"] = {"p_c_inf": f.p_inf, "p_c_inf_err": f.p_inf_err, "chi2": f.chi2, "dof": f.dof,
+                              "C0_C1_alpha": None if law is None else law[0]}
+    best = fits["W>=12"]
+    return {
+        "metric": "p_c_inf", "value": best["p_c_inf"], "unit": "probability", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": None, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bits", "data": "synthetic",
+        "config": {"workload": "finite-size scaling, W in {4..32} x W/L in {2..1/8}, seed 6",
+                   "sizes": len(sizes), "configurations": n_cfg},
+        "configs_per_s": n_cfg / t,
+        "paper": {"p_c_inf": 0.1533, "p_c_inf_err": 0.0013, "alpha": -1.23, "C0": -0.83, "C1": 0.31},
+        "fits": fits,
+        "p_c": {f"{k[0]},{k[1]}": [v[0].p_c, v[0].p_c_err] for k, v in sorted(curves.items())},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,7 +476,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--configs-per-p", type=int, default=N_CFG,
                     help="smaller cases for profiling only; the benchmark workload is 10^4")
-    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch", "serving"])
+    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch", "serving", "fss"])
     ap.add_argument("--serve-queries", type=int, default=24)
     ap.add_argument("--serve-budget-gb", type=int, default=128)
     ap.add_argument("--large-configs", type=int, default=64)
@@ -466,7 +499,7 @@ def main():
         torch.cuda.set_device(0)
         pc.build()
         pc.load()
-        fn = {"large": run_large, "batch": run_batch, "serving": run_serving}[args.workload]
+        fn = {"large": run_large, "batch": run_batch, "serving": run_serving, "fss": run_fss}[args.workload]
         print(json.dumps(fn(args, pc, torch)), flush=True)
         return 0
 
