@@ -121,7 +121,10 @@ pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t 
  * n_percolating (int64) and Pi (= n_percolating / n_configs) are optional.
  * Outputs are host pointers unless flags has PC_OUT_DEVICE.  flags may also
  * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, and PC_BITS_ONLY.
- * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
+ * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL, and
+ * PC_ERR_TIMEOUT if a bounded device wait of the streamed solver expires
+ * (host outputs only: with PC_OUT_DEVICE the call returns before the device
+ * work ends).
  */
 pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed,
                      int64_t config_begin, int64_t n_configs,
