@@ -294,14 +294,12 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
 }
 
 
-// Ring state carried across the FP units of one CTA.  Planes take ring slots
-// in the order they are copied, continuing across units: the n-th plane of
-// the CTA (counting from 0) is in slot n mod nring, and its barrier
-// completes with parity (n / nring) & 1.
+// Ring state carried across the FP units of one CTA.
 struct Ring {
-  uint32_t nw;  // planes waited for (identical in all threads while no wait expires)
-  uint32_t ni;  // thread 0: planes copied
-  bool dead;    // this thread saw a wait expire: no further waits or copies
+  uint32_t ph;    // expected parity of each slot's barrier (identical in all threads)
+  uint32_t pend;  // thread 0: slots with a copy issued and not yet waited for
+  int base;       // slot of the next unit's first plane (identical in all threads)
+  bool dead;      // this thread saw a wait expire: no further waits or copies
 };
 
 // One FP unit: strips [k0, k0 + kCols) (one per thread) over layers
@@ -309,8 +307,9 @@ struct Ring {
 // (planes t+1 and older are already in registers).  The segment [lo, hi) of
 // each plane the chunk touches, and the same byte range of the degree layer
 // three planes below it, are copied into the next ring slot by thread 0
-// (cp.async.bulk; an mbarrier per slot counts the bytes), in the slot order
-// of struct Ring.  After each pair of layers a block barrier
+// (cp.async.bulk; an mbarrier per slot counts the bytes).  Planes take ring
+// slots in the order they are copied, continuing across units: plane t0+1 of
+// this unit is in slot rg.base.  After each pair of layers a block barrier
 // frees the slots of the two planes the pair is done with and thread 0
 // refills them nring planes further on, so the copies run at least nring-3
 // layers ahead of their use.  A wait that expires sets
@@ -357,7 +356,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   // thread 0: copy plane pl (and the degree layer pl - 3) into slot sl
   auto issue = [&](int pl, int sl) {
     if (tid != 0 || rg.dead || pl > last) return;
-    ++rg.ni;
+    rg.pend |= 1u << sl;
     const int lay = pl - 3;
     const bool with_dg = lay >= t0;
     fence_proxy_async_shared();
@@ -365,27 +364,23 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     bulk_g2s(ring + (size_t)sl * cap, src + (size_t)pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
     if (with_dg) bulk_g2s(dring + (size_t)sl * cap, v.dg + (size_t)lay * P + lo_al, (unsigned)seg, &full[sl]);
   };
-  // the next plane to wait for: its slot ws and barrier parity wp
-  int ws = (int)(rg.nw % (uint32_t)nring);
-  uint32_t wp = (rg.nw / (uint32_t)nring) & 1u;
-  auto wait = [&](int sl) {  // sl == ws: the planes are waited for in order
-    if (!rg.dead) {
-      if (mbar_wait(&full[sl], wp)) {
-        ++rg.nw;
-      } else {
-        rg.dead = true; *abort = 1; atomicOr(x.error, 2);
-      }
+  auto wait = [&](int sl) {
+    if (rg.dead) return;
+    if (!mbar_wait(&full[sl], (rg.ph >> sl) & 1u)) {
+      rg.dead = true; *abort = 1; atomicOr(x.error, 2);
+      return;
     }
-    if (++ws == nring) { ws = 0; wp ^= 1u; }
+    rg.ph ^= 1u << sl;
+    rg.pend &= ~(1u << sl);
   };
   const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
   const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al, g0 = b - lo_al;
 
   {
-    int sl = ws;
+    int sl = rg.base;
     for (int i = 1; i <= nring; ++i, sl = inc(sl)) issue(t0 + i, sl);
   }
-  const int s1 = ws;       // plane t0 + 1
+  const int s1 = rg.base;  // plane t0 + 1
   int s2 = inc(s1);        // plane t + 2
   int s3 = inc(s2);        // plane t + 3
   wait(s1);
@@ -403,13 +398,12 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   issue(t0 + 1 + nring, s1);
   // layers in pairs: one block barrier frees the two planes the pair is done with
   int t = t0;
-  float* out = dst + (size_t)(t0 + 2) * P;  // plane of layer t in dst
   for (;;) {
     wait(s3);
     {
       load_runs(B, ring + (size_t)s3 * cap, u0, d0, c0);
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      strip_emit_deg(A, B, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, out, b,
+      strip_emit_deg(A, B, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
                      dg[0], dg[1], dg[2], inv);
       up2 = A.U[2]; dp2 = A.D[2];
 #pragma unroll
@@ -417,7 +411,6 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     }
     const int fa = s2;  // plane t + 2: done
     s2 = s3; s3 = inc(s3);
-    out += P;
     if (++t >= t1) {
       __syncthreads();
       issue(t + 1 + nring, fa);
@@ -427,7 +420,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     {
       load_runs(A, ring + (size_t)s3 * cap, u0, d0, c0);
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      strip_emit_deg(B, A, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, out, b,
+      strip_emit_deg(B, A, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
                      dg[0], dg[1], dg[2], inv);
       up2 = B.U[2]; dp2 = B.D[2];
 #pragma unroll
@@ -435,12 +428,13 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     }
     const int fb = s2;  // plane t + 2: done
     s2 = s3; s3 = inc(s3);
-    out += P;
     __syncthreads();    // planes t + 1 and t + 2 are free
     issue(t + 1 + nring, fa);
     issue(t + 2 + nring, fb);
     if (++t >= t1) break;
   }
+  // s2 now holds plane t1 + 2 (the last); the next unit continues after it
+  rg.base = inc(s2);
 }
 
 __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
@@ -460,7 +454,7 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
     mbar_fence_init();
   }
   __syncthreads();
-  Ring rg{0u, 0u, false};
+  Ring rg{0u, 0u, 0, false};
   const int total = x.pre[x.K];
   // units are taken from a tick-wide counter (double-buffered broadcast: one
   // block barrier per unit)
@@ -497,8 +491,8 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
       __syncthreads();
       if (s_abort) {  // a wait expired: let the copies in flight land (bounded), then stop
         if (tid == 0)
-          for (uint32_t n = rg.nw; n < rg.ni; ++n)
-            mbar_wait(&bars[n % (uint32_t)x.nring], (n / (uint32_t)x.nring) & 1u);
+          for (int sl = 0; sl < x.nring; ++sl)
+            if ((rg.pend >> sl) & 1u) mbar_wait(&bars[sl], (rg.ph >> sl) & 1u);
         return;
       }
     } else if (kind == U_BITS) {
