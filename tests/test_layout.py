@@ -65,3 +65,12 @@ def test_strip_gathers_hit_the_right_neighbours(W):
                 got = value_at(starts[name] + j + kk)
                 want = idx.get((int(q[a]) + dq, int(r[a]) + dr), -1)
                 assert got == want, (W, st, j, d, got, want)
+
+
+def test_static_entry_point_tables_cover_its_widest_lattice():
+    # pc_inspect_static keeps the layout of every accepted width (W <= 51) in
+    # fixed tables of 9216 plane entries and 9216 / 3 + 2 strips
+    for W in range(0, 52):
+        lay = pc.pc_lattice_layout(W)
+        assert lay["P"] <= 9216, (W, lay["P"])
+        assert lay["n_strips"] <= 9216 // 3 + 2, (W, lay["n_strips"])
