@@ -305,16 +305,31 @@ void worker_main(pc_server* s) {
       std::lock_guard<std::mutex> lk(s->mu);
       for (uint64_t id : running) if (s->tickets[id].kind == 1) streamed = true;
     }
+    pc_status dev_rc = PC_OK;
     while (streamed && inflight < 2) {
       const int b = (int)(next_seq & 1);
       const int* ph = nullptr;
       const unsigned long long* qd = nullptr;
-      if (server_engine_run_chunk(s->E, s->tick) || server_engine_status(s->E, s->tick, b, &ph, &qd) ||
-          cudaEventRecord(ev[b], s->tick) != cudaSuccess) {
-        break;
-      }
+      if ((dev_rc = server_engine_run_chunk(s->E, s->tick)) ||
+          (dev_rc = server_engine_status(s->E, s->tick, b, &ph, &qd))) break;
+      const cudaError_t e = cudaEventRecord(ev[b], s->tick);
+      if (e != cudaSuccess) { dev_rc = cuda_fail(e, "server: record tick event"); break; }
       ++next_seq;
       ++inflight;
+    }
+    if (dev_rc) {
+      // the device loop cannot go on: every query still queued or running
+      // fails with the CUDA error instead of waiting forever
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto& kv : s->tickets)
+        if (kv.second.state == T_PENDING || kv.second.state == T_RUNNING) {
+          kv.second.state = T_FAILED;
+          kv.second.status = dev_rc;
+        }
+      s->pending.clear();
+      s->stop = true;
+      s->cv_done.notify_all();
+      break;
     }
     const int* phases = nullptr;
     const unsigned long long* qdone = nullptr;
