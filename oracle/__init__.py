@@ -72,9 +72,10 @@ def _load():
             lib.oracle_first_passage.argtypes = [i32, i32, vp, ctypes.c_int32, vp, vp]
             lib.oracle_first_passage_dense.argtypes = [i32, vp, i32, i32, i32, vp]
             lib.oracle_max_threads.argtypes = []
+            lib.oracle_critical_words.argtypes = [i32, i32, vp, vp, u64, i64, i64, i32, vp]
             for f in ("oracle_lattice_info", "oracle_columns", "oracle_adjacency",
                       "oracle_occupancy", "oracle_site_words", "oracle_inspect", "oracle_first_passage",
-                      "oracle_first_passage_dense", "oracle_max_threads"):
+                      "oracle_first_passage_dense", "oracle_max_threads", "oracle_critical_words"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -148,6 +149,28 @@ def site_words(W: int, L: int, seed: int, cfg0: int, n: int) -> np.ndarray:
     w = np.zeros((n, N), np.uint32)
     _check(_load().oracle_site_words(W, L, int(seed) & (2**64 - 1), cfg0, n, _ptr(w)), "site_words")
     return w
+
+
+def critical_words(W: int, L: int, seed: int, cfg0: int, n: int, adjacency=None,
+                   threads: int = 0) -> np.ndarray:
+    """Critical word w* of each configuration [n] (uint64): it percolates at p
+    exactly when threshold(p) > w*, so Pi(p) for every p comes from one pass
+    (Sec. II.B spanning path, union-find in increasing word order).
+    ``adjacency`` = (nbr [N][14], count [N]) as ``adjacency`` returns it, to
+    run another neighbour table; None = the lattice's own."""
+    _, N = lattice_info(W, L)
+    out = np.zeros(n, np.uint64)
+    nbr = cnt = None
+    if adjacency is not None:
+        nbr = np.ascontiguousarray(adjacency[0], dtype=np.int64)
+        cnt = np.ascontiguousarray(adjacency[1], dtype=np.int32)
+        if nbr.shape != (N, 14) or cnt.shape != (N,) or np.any(cnt > 14) or np.any(cnt < 0):
+            raise ValueError("adjacency must be ([N][14], [N]) with counts <= 14")
+        if N and (nbr.max() >= N or any(np.any(nbr[i, :c] < 0) for i, c in enumerate(cnt) if c)):
+            raise ValueError("adjacency entries out of range")
+    _check(_load().oracle_critical_words(W, L, _ptr(nbr), _ptr(cnt), int(seed) & (2**64 - 1), cfg0, n,
+                                          threads, _ptr(out)), "critical_words")
+    return out
 
 
 def occupancy_fixed(W: int, L: int, n_metallic: int, seed: int, cfg0: int, n: int) -> np.ndarray:

@@ -35,6 +35,9 @@
  *     bounds the step count.
  *   - Independent verdict routes: breadth-first search (the shortest spanning
  *     path of Sec. II.B is the BFS distance) and union-find.
+ *   - Critical word per configuration: union-find over the sites in
+ *     increasing order of their random word; it gives the verdict at every p
+ *     at once (used by the finite-size-scaling pin of the lattice, Sec. III).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   * mu_0 is uniform over the metallic sites of the start layer t = 0.
@@ -555,6 +558,81 @@ int oracle_site_words(int W, int L, uint64_t seed, int64_t cfg0, int64_t n, uint
     }
   }
   return OR_OK;
+}
+
+static int cmp_u64(const void *x, const void *y) {
+  uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+  return a < b ? -1 : a > b;
+}
+
+/*
+ * Critical word of each configuration cfg0..cfg0+n-1 (out: [n]).  With the
+ * coupled draws above, site i is metallic at p exactly when its word is below
+ * T(p), so a configuration percolates at p exactly when T(p) exceeds its
+ * critical word w*: the word of the site whose addition, in increasing order
+ * of (word, site index), first joins the start face t = 0 to the end face
+ * t = L-1 through metallic sites (Sec. II.B: percolation is the existence of
+ * such a path).  One pass gives the verdict at every p, so Pi(p) of Eq. (5)
+ * is the empirical distribution of w* / 2^32.
+ * nbr/count: the adjacency to use, laid out as oracle_adjacency writes it
+ * ([N][14], -1 padded, and the count per site); NULL = the lattice's own.
+ * w* is 2^32 only if no spanning path exists with every site metallic, which
+ * the axial contacts of each column rule out.
+ */
+int oracle_critical_words(int W, int L, const int64_t *nbr, const int32_t *count, uint64_t seed,
+                          int64_t cfg0, int64_t n, int threads, uint64_t *out) {
+  if (check_args(W, L) || cfg0 < 0 || n < 0 || cfg0 + n > 4294967296LL) return OR_ERR_ARG;
+  lattice_t lat;
+  int st = lattice_build(&lat, W, L);
+  if (st) return st;
+  const int64_t N = lat.N, A = lat.A;
+  if (N >= (1LL << 32)) { lattice_free(&lat); return OR_ERR_ARG; }
+  int err = OR_OK;
+#ifdef _OPENMP
+  int nt = threads > 0 ? threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+  for (int64_t c = 0; c < n; ++c) {
+    uint32_t *w = malloc(sizeof(uint32_t) * N);
+    uint64_t *key = malloc(sizeof(uint64_t) * N);
+    int64_t *parent = malloc(sizeof(int64_t) * (N + 2));
+    uint8_t *on = calloc(N, 1);
+    if (!w || !key || !parent || !on) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+      err = OR_ERR_OOM;
+      free(w); free(key); free(parent); free(on);
+      continue;
+    }
+    oracle_site_words(W, L, seed, cfg0 + c, 1, w);
+    for (int64_t i = 0; i < N; ++i) key[i] = ((uint64_t)w[i] << 32) | (uint64_t)i;
+    qsort(key, (size_t)N, sizeof(uint64_t), cmp_u64);
+    const int64_t TOP = N, BOT = N + 1;
+    for (int64_t i = 0; i < N + 2; ++i) parent[i] = i;
+    uint64_t crit = 1ULL << 32;
+    int64_t nb[32];
+    for (int64_t j = 0; j < N; ++j) {
+      const int64_t i = (int64_t)(key[j] & 0xffffffffu), t = i / A;
+      on[i] = 1;
+      if (t == 0) { int64_t x = uf_find(parent, i), y = uf_find(parent, TOP); if (x != y) parent[x] = y; }
+      if (t == L - 1) { int64_t x = uf_find(parent, i), y = uf_find(parent, BOT); if (x != y) parent[x] = y; }
+      int m;
+      if (nbr) {
+        m = count[i];
+        for (int k = 0; k < m; ++k) nb[k] = nbr[i * 14 + k];
+      } else {
+        m = site_neighbours(&lat, i, nb);
+      }
+      for (int k = 0; k < m; ++k)
+        if (on[nb[k]]) { int64_t x = uf_find(parent, i), y = uf_find(parent, nb[k]); if (x != y) parent[x] = y; }
+      if (uf_find(parent, TOP) == uf_find(parent, BOT)) { crit = key[j] >> 32; break; }
+    }
+    out[c] = crit;
+    free(w); free(key); free(parent); free(on);
+  }
+  lattice_free(&lat);
+  return err;
 }
 
 enum { MODE_MARKOV = 0, MODE_BFS = 1, MODE_UNIONFIND = 2, MODE_MARKOV_FULL = 3 };
