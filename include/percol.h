@@ -120,7 +120,8 @@ pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t 
  *               whose reached set did not grow; 0 if no start site is metallic
  * n_percolating (int64) and Pi (= n_percolating / n_configs) are optional.
  * Outputs are host pointers unless flags has PC_OUT_DEVICE.  flags may also
- * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, and PC_BITS_ONLY.
+ * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, and PC_BITS_ONLY; any other
+ * bit is PC_ERR_ARG.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL, and
  * PC_ERR_TIMEOUT if a bounded device wait of the streamed solver expires
  * (host outputs only: with PC_OUT_DEVICE the call returns before the device
@@ -182,7 +183,7 @@ typedef struct pc_result {
  * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
- * applies to every query of the batch.
+ * applies to every query of the batch; any other flag bit is PC_ERR_ARG.
  * Results equal those of pc_inspect on each query.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
  */

@@ -85,6 +85,9 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
                        int32_t* first_hit, float* mass, int32_t* m_stop,
                        int64_t* n_percolating, double* Pi, int32_t flags, void* stream) {
   const bool dev_out = (flags & PC_OUT_DEVICE) != 0;
+  if (flags & ~(PC_OUT_DEVICE | PC_MODE_RESIDENT | PC_MODE_STREAM | PC_BITS_ONLY)) {
+    set_error("unknown flag bits"); return PC_ERR_ARG;
+  }
   if (!verdicts && n > 0) { set_error("verdicts must not be NULL"); return PC_ERR_ARG; }
   if (dev_out && Pi) { set_error("Pi must be NULL with PC_OUT_DEVICE"); return PC_ERR_ARG; }
   if ((flags & PC_MODE_RESIDENT) && (flags & PC_MODE_STREAM)) { set_error("conflicting mode flags"); return PC_ERR_ARG; }

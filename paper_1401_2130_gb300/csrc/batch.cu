@@ -279,6 +279,7 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
                                   void* cuda_stream) {
   NvtxRange nvtx_("pc_batch_run");
   if (nq < 0 || (nq > 0 && !q)) { set_error("pc_batch_run: bad query array"); return PC_ERR_ARG; }
+  if (flags & ~(PC_OUT_DEVICE | PC_ASYNC | PC_BITS_ONLY)) { set_error("pc_batch_run: unknown flag bits"); return PC_ERR_ARG; }
   const bool dev_out = (flags & PC_OUT_DEVICE) != 0, async = (flags & PC_ASYNC) != 0;
   if (async && (!dev_out || out)) { set_error("PC_ASYNC needs PC_OUT_DEVICE and out == NULL"); return PC_ERR_ARG; }
   for (int64_t i = 0; i < nq; ++i) {

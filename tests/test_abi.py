@@ -84,6 +84,29 @@ def test_inspect_argument_errors_without_gpu(lib):
     pi = ctypes.c_double()
     assert lib.pc_inspect(4, 16, 0.2, 1, 0, 4, ctypes.addressof(v), None, None, None, None,
                           ctypes.addressof(pi), pc.PC_OUT_DEVICE, None) == pc.PC_ERR_ARG
+    # both solvers forced, and flag bits the call does not define
+    for flags in (pc.PC_MODE_RESIDENT | pc.PC_MODE_STREAM, pc.PC_ASYNC, 0x4, 0x80, 1 << 30):
+        assert lib.pc_inspect(4, 16, 0.2, 1, 0, 4, ctypes.addressof(v), None, None, None, None,
+                              None, flags, None) == pc.PC_ERR_ARG, flags
+        assert lib.pc_inspect_occupancy(4, 16, ctypes.addressof(v), 4, ctypes.addressof(v), None,
+                                        None, None, None, None, flags, None) == pc.PC_ERR_ARG, flags
+
+
+def test_batch_argument_errors_without_gpu(lib):
+    import ctypes
+    v = (ctypes.c_uint8 * 4)()
+    good = pc.PcQuery(W=4, L=16, p=0.2, seed=1, config_begin=0, n_configs=4,
+                      verdicts=ctypes.addressof(v))
+    for flags in (pc.PC_MODE_STREAM, 0x4, 1 << 30):
+        assert lib.pc_batch_run(ctypes.addressof(good), 1, None, flags, None) == pc.PC_ERR_ARG, flags
+    # PC_ASYNC needs device outputs and no host summaries
+    assert lib.pc_batch_run(ctypes.addressof(good), 1, None, pc.PC_ASYNC, None) == pc.PC_ERR_ARG
+    for q in (dict(W=256), dict(L=0), dict(p=1.01), dict(n_configs=-1), dict(config_begin=2**32),
+              dict(verdicts=None)):
+        bad = pc.PcQuery(**{**dict(W=4, L=16, p=0.2, seed=1, config_begin=0, n_configs=4,
+                                   verdicts=ctypes.addressof(v)), **q})
+        assert lib.pc_batch_run(ctypes.addressof(bad), 1, None, 0, None) == pc.PC_ERR_ARG, q
+    assert lib.pc_batch_run(None, 3, None, 0, None) == pc.PC_ERR_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path):
