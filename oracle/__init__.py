@@ -73,9 +73,11 @@ def _load():
             lib.oracle_first_passage_dense.argtypes = [i32, vp, i32, i32, i32, vp]
             lib.oracle_max_threads.argtypes = []
             lib.oracle_critical_words.argtypes = [i32, i32, vp, vp, u64, i64, i64, i32, vp]
+            lib.oracle_first_passage_lazy.argtypes = [i32, i32, vp, ctypes.c_int32, dbl, vp]
             for f in ("oracle_lattice_info", "oracle_columns", "oracle_adjacency",
                       "oracle_occupancy", "oracle_site_words", "oracle_inspect", "oracle_first_passage",
-                      "oracle_first_passage_dense", "oracle_max_threads", "oracle_critical_words"):
+                      "oracle_first_passage_dense", "oracle_max_threads", "oracle_critical_words",
+                      "oracle_first_passage_lazy"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -248,6 +250,17 @@ def first_passage(W: int, L: int, occ: np.ndarray, mmax: int):
     _check(_load().oracle_first_passage(W, L, _ptr(occ), mmax, _ptr(fw), _ptr(bw)),
            "first_passage")
     return fw, bw
+
+
+def first_passage_lazy(W: int, L: int, occ: np.ndarray, mmax: int, hold: float) -> np.ndarray:
+    """Forward a_m, m = 1..mmax, of the lazy walk hold * I + (1 - hold) * P
+    (the self-loop remark of Sec. II.B); hold in [0, 1)."""
+    _, N = lattice_info(W, L)
+    occ = np.ascontiguousarray(occ, dtype=np.uint8).reshape(N)
+    fw = np.zeros(mmax, np.float64)
+    _check(_load().oracle_first_passage_lazy(W, L, _ptr(occ), mmax, float(hold), _ptr(fw)),
+           "first_passage_lazy")
+    return fw
 
 
 def first_passage_dense(P: np.ndarray, j0: int, i0: int, mmax: int) -> np.ndarray:

@@ -35,6 +35,8 @@
  *     bounds the step count.
  *   - Independent verdict routes: breadth-first search (the shortest spanning
  *     path of Sec. II.B is the BFS distance) and union-find.
+ *   - The lazy walk of the self-loop remark (Sec. II.B): forward first
+ *     passage under hold * I + (1 - hold) * P.
  *   - Critical word per configuration: union-find over the sites in
  *     increasing order of their random word; it gives the verdict at every p
  *     at once (used by the finite-size-scaling pin of the lattice, Sec. III).
@@ -763,6 +765,50 @@ int oracle_first_passage(int W, int L, const uint8_t *occ, int32_t mmax,
   }
 out:
   free(mu); free(mu2); free(f); free(f2); free(mu0);
+  markov_free(&M);
+  lattice_free(&lat);
+  return st;
+}
+
+/*
+ * The lazy walk of the self-loop remark in Sec. II.B: at every step the
+ * electron stays on its site with probability hold and otherwise moves as
+ * Eq. (2) says, i.e. the chain hold * I + (1 - hold) * P over the metallic
+ * sites (the detector stays absorbing).  Forward first-passage probabilities
+ * a_m, m = 1..mmax, as oracle_first_passage computes them for P:
+ *   a_m = (1 - hold) sum_i mu_{m-1}(i) P_{i j1},
+ *   mu_m = hold mu_{m-1} + (1 - hold) mu_{m-1} ^(j1)P.
+ * hold in [0, 1).
+ */
+int oracle_first_passage_lazy(int W, int L, const uint8_t *occ, int32_t mmax, double hold,
+                              double *a_forward) {
+  if (check_args(W, L) || mmax < 0 || !(hold >= 0.0 && hold < 1.0)) return OR_ERR_ARG;
+  lattice_t lat;
+  int st = lattice_build(&lat, W, L);
+  if (st) return st;
+  markov_t M;
+  st = markov_build(&lat, occ, &M);
+  if (st) { lattice_free(&lat); return st; }
+  int64_t Np = M.Np;
+  double *mu = calloc(Np + 1, sizeof(double)), *mu2 = calloc(Np + 1, sizeof(double));
+  if (!mu || !mu2) { st = OR_ERR_OOM; goto out; }
+  int64_t n0 = 0;
+  for (int64_t k = 0; k < Np; ++k) n0 += M.is_start[k];
+  for (int64_t k = 0; k < Np; ++k) mu[k] = (n0 && M.is_start[k]) ? 1.0 / (double)n0 : 0.0;
+  for (int32_t m = 1; m <= mmax; ++m) {
+    double a = 0.0;
+    for (int64_t k = 0; k < Np; ++k)
+      for (int64_t e = M.ptr[k]; e < M.ptr[k + 1]; ++e)
+        if (M.col[e] == Np) a += mu[k] * M.val[e];
+    a_forward[m - 1] = (1.0 - hold) * a;
+    for (int64_t k = 0; k < Np; ++k) mu2[k] = hold * mu[k];
+    for (int64_t k = 0; k < Np; ++k)
+      for (int64_t e = M.ptr[k]; e < M.ptr[k + 1]; ++e)
+        if (M.col[e] != Np) mu2[M.col[e]] += (1.0 - hold) * mu[k] * M.val[e];
+    { double *t = mu; mu = mu2; mu2 = t; }
+  }
+out:
+  free(mu); free(mu2);
   markov_free(&M);
   lattice_free(&lat);
   return st;

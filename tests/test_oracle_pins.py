@@ -461,3 +461,55 @@ def test_fixed_count_is_uniform_over_subsets():
     expected = n / comb(7, 3)
     chi2 = float(((counts - expected) ** 2 / expected).sum())
     assert chi2 < 70.0  # 34 degrees of freedom: P(chi2 > 70) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# The lazy walk of the self-loop remark (Sec. II.B): staying put with
+# probability s does not change percolation.  Under s I + (1 - s) P the first
+# passage at the shortest spanning length needs a move at every step, so it is
+# (1 - s)^m times the plain one, and the probability of ever being absorbed is
+# unchanged.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.9])
+def test_lazy_walk_on_fig2(s):
+    P = _load_fig2()
+    Ps = s * np.eye(7) + (1 - s) * P
+    f = oracle.first_passage_dense(Ps, j0=6, i0=0, mmax=int(1500 / (1 - s)))
+    assert np.all(f[:5] == 0.0)
+    assert f[5] == pytest.approx((1 - s) ** 6 / 32, rel=1e-13)
+    assert f.sum() == pytest.approx(1.0, abs=1e-9)  # the chain is connected
+
+
+@pytest.mark.parametrize("s", [0.0, 0.25, 0.5, 0.9])
+def test_lazy_walk_keeps_first_hit_and_scales_its_mass(s):
+    W, L = 2, 5
+    occ = oracle.occupancy(W, L, 0.55, 21, 0, 40)
+    r = oracle.inspect(W, L, occ=occ, mode="markov")
+    for c in range(40):
+        plain, _ = oracle.first_passage(W, L, occ[c], 25)
+        lazy = oracle.first_passage_lazy(W, L, occ[c], 25, s)
+        if s == 0.0:
+            assert np.array_equal(lazy, plain)
+        if r["verdict"][c]:
+            m = r["first_hit"][c]
+            assert np.all(lazy[: m - 1] == 0.0) and lazy[m - 1] > 0
+            assert lazy[m - 1] == pytest.approx((1 - s) ** m * r["mass"][c], rel=1e-12)
+        else:
+            assert np.all(lazy == 0.0)
+
+
+def test_lazy_walk_absorbs_the_same_total():
+    W, L = 1, 4
+    occ = oracle.occupancy(W, L, 0.7, 5, 0, 12)
+    for c in range(12):
+        plain, _ = oracle.first_passage(W, L, occ[c], 3000)
+        lazy = oracle.first_passage_lazy(W, L, occ[c], 6000, 0.5)
+        assert lazy.sum() == pytest.approx(plain.sum(), abs=1e-10)
+
+
+def test_lazy_walk_rejects_hold_outside_unit_interval():
+    occ = oracle.occupancy(1, 3, 0.5, 1, 0, 1)[0]
+    for bad in (-0.1, 1.0, float("nan")):
+        with pytest.raises(RuntimeError):
+            oracle.first_passage_lazy(1, 3, occ, 5, bad)
