@@ -300,6 +300,24 @@ pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t seed,
 pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
                             int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol);
 
+/*
+ * The lazy walk of the self-loop remark in Sec. II.B: at every step the
+ * electron stays on its site with probability hold, otherwise it moves as
+ * Eq. (2) says (the chain hold * I + (1 - hold) * P).  Percolation, first_hit
+ * and m_stop do not change, and the probability of arriving at the first
+ * hit is the plain one times (1 - hold)^first_hit (each of the first_hit
+ * moves of a shortest spanning walk now happens with probability 1 - hold).
+ * This writes that mass from pc_inspect's first_hit and mass outputs:
+ * mass_lazy[i] = mass[i] * (1 - hold)^first_hit[i] (computed in FP64,
+ * stored as FP32), 0 where first_hit[i] <= 0.  All three arrays have
+ * n_configs entries and are host buffers (the call then synchronises
+ * cuda_stream), or device buffers with flags = PC_OUT_DEVICE (asynchronous).
+ * mass_lazy may alias mass.  Errors: PC_ERR_ARG (hold outside [0, 1),
+ * n_configs < 0, a NULL buffer, other flag bits), PC_ERR_CUDA.
+ */
+pc_status pc_lazy_mass(const int32_t* first_hit, const float* mass, int64_t n_configs,
+                       double hold, float* mass_lazy, int32_t flags, void* cuda_stream);
+
 /* Release cached lattice tables and scratch of every device. */
 pc_status pc_shutdown(void);
 

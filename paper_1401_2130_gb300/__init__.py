@@ -52,6 +52,7 @@ SIGNATURES = {
     "pc_server_get_stats": [_vp, _vp],
     "pc_server_destroy": [_vp],
     "pc_lattice_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pc_lazy_mass": [_vp, _vp, _i64, _dbl, _vp, _i32, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
 }
@@ -210,6 +211,32 @@ def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs
         o["n_percolating"] = npc.value
         o["Pi"] = pi.value
     return o
+
+
+def pc_lazy_mass(first_hit, mass, hold: float, *, out=None, stream=None):
+    """Mass at the first hit under the lazy walk hold * I + (1 - hold) * P
+    (the self-loop remark of Sec. II.B), from pc_inspect's first_hit and mass:
+    mass * (1 - hold)^first_hit, 0 where first_hit <= 0.  numpy arrays in,
+    numpy out (synchronising); torch CUDA tensors in, a CUDA tensor out
+    written asynchronously on ``stream``."""
+    device = hasattr(mass, "is_cuda") and mass.is_cuda
+    n = int(mass.shape[0])
+    if device:
+        import torch
+        assert first_hit.is_cuda and first_hit.dtype == torch.int32 and mass.dtype == torch.float32
+        assert first_hit.is_contiguous() and mass.is_contiguous() and first_hit.shape[0] == n
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=mass.device)
+    else:
+        first_hit = np.ascontiguousarray(first_hit, dtype=np.int32)
+        mass = np.ascontiguousarray(mass, dtype=np.float32)
+        if first_hit.shape[0] != n:
+            raise ValueError("first_hit and mass differ in length")
+        if out is None:
+            out = np.zeros(n, np.float32)
+    _check(load().pc_lazy_mass(_ptr(first_hit), _ptr(mass), n, float(hold), _ptr(out),
+                               PC_OUT_DEVICE if device else 0, _stream_handle(stream)))
+    return out
 
 
 def pc_inspect_occupancy(W: int, L: int, occ_bits, *, device: bool = False,

@@ -92,6 +92,21 @@ def test_inspect_argument_errors_without_gpu(lib):
                                         None, None, None, None, flags, None) == pc.PC_ERR_ARG, flags
 
 
+def test_lazy_mass_argument_errors_without_gpu(lib):
+    import ctypes
+    fh = (ctypes.c_int32 * 4)()
+    m = (ctypes.c_float * 4)()
+    o = (ctypes.c_float * 4)()
+    a = [ctypes.addressof(fh), ctypes.addressof(m)]
+    for hold in (-0.1, 1.0, 1.5, float("nan")):
+        assert lib.pc_lazy_mass(*a, 4, hold, ctypes.addressof(o), 0, None) == pc.PC_ERR_ARG, hold
+    assert lib.pc_lazy_mass(*a, -1, 0.5, ctypes.addressof(o), 0, None) == pc.PC_ERR_ARG
+    assert lib.pc_lazy_mass(None, a[1], 4, 0.5, ctypes.addressof(o), 0, None) == pc.PC_ERR_ARG
+    assert lib.pc_lazy_mass(*a, 4, 0.5, None, 0, None) == pc.PC_ERR_ARG
+    assert lib.pc_lazy_mass(*a, 4, 0.5, ctypes.addressof(o), pc.PC_BITS_ONLY, None) == pc.PC_ERR_ARG
+    assert lib.pc_lazy_mass(None, None, 0, 0.5, None, 0, None) == pc.PC_OK  # nothing to do
+
+
 def test_batch_argument_errors_without_gpu(lib):
     import ctypes
     v = (ctypes.c_uint8 * 4)()
