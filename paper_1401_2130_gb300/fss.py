@@ -172,7 +172,13 @@ def scan(sizes, seed: int, n_coarse: int = 256, n_fine: int = 1024, fine_points:
     ``coarse_p`` (n_coarse configurations per point) locates the transition;
     a fine pass of ``fine_points`` values over p_c +- 3T (n_fine
     configurations each) is fitted with Eq. (5).  Returns
-    {(W, L): (FDFit, p, k, n)} of the fine pass."""
+    {(W, L): (FDFit, p, k, n)} of the fine pass.
+
+    Each fine point inspects its own configurations (j * n_fine onwards for
+    point j): the occupancy stream couples the draws of one configuration
+    across p, so reusing configurations would make the counts of
+    neighbouring points correlated, and the binomial errors of Eq. (5)'s fit
+    -- which assume independent counts -- too small."""
     sizes = [tuple(s) for s in sizes]
     specs = [(W, L, p, seed, 0, n_coarse) for (W, L) in sizes for p in coarse_p]
     k = measure(specs)
@@ -184,7 +190,7 @@ def scan(sizes, seed: int, n_coarse: int = 256, n_fine: int = 1024, fine_points:
         lo, hi = max(f.p_c - half, 1e-4), min(f.p_c + half, 1.0)
         grid = np.round(np.linspace(lo, hi, fine_points), 6)
         grids[(W, L)] = grid
-        fine_specs += [(W, L, float(p), seed, 0, n_fine) for p in grid]
+        fine_specs += [(W, L, float(p), seed, j * n_fine, n_fine) for j, p in enumerate(grid)]
     k2 = measure(fine_specs)
     out = {}
     for i, (W, L) in enumerate(sizes):

@@ -1,5 +1,7 @@
 """Finite-size-scaling analysis (Sec. III, Eqs. (5)-(9)) on synthetic data
 with known parameters, and Eq. (9) against the number the paper prints."""
+import os
+
 import numpy as np
 import pytest
 
@@ -80,3 +82,74 @@ def test_decay_rate_recovers_exponential():
     assert f.lam == pytest.approx(0.0123, rel=1e-4)
     # fully percolating over the range: no decay
     assert fss.decay_rate(L, n, n).lam == 0.0
+
+
+# ---------------------------------------------------------------------------
+# The scan and length-scan orchestration, with the oracle's counts in place of
+# the GPU batch (the GPU verdicts equal the oracle's bit for bit): a
+# configuration percolates at p exactly when T(p) exceeds its critical word.
+# ---------------------------------------------------------------------------
+
+def _oracle_counts(monkeypatch):
+    import oracle
+    threads = os.cpu_count() or 1
+    words = {}
+    seen = []
+
+    def measure(specs):
+        out = []
+        for (W, L, p, seed, b, n) in specs:
+            seen.append((W, L, p, seed, b, n))
+            have = words.get((W, L, seed), np.zeros(0, np.uint64))
+            if have.size < b + n:
+                extra = oracle.critical_words(W, L, seed, have.size, b + n - have.size, threads=threads)
+                have = words[(W, L, seed)] = np.concatenate([have, extra])
+            out.append(int((have[b:b + n] < oracle.threshold(p)).sum()))
+        return out
+
+    monkeypatch.setattr(fss, "measure", measure)
+    return words, seen
+
+
+def test_scan_fine_points_use_disjoint_configurations(monkeypatch):
+    _, seen = _oracle_counts(monkeypatch)
+    fss.scan([(4, 8), (6, 6)], seed=3, n_coarse=64, n_fine=128, fine_points=7)
+    for size in ((4, 8), (6, 6)):
+        fine = [s for s in seen if s[:2] == size and s[5] == 128]
+        assert len(fine) == 7
+        starts = sorted(s[4] for s in fine)
+        assert starts == [j * 128 for j in range(7)]
+
+
+def test_scan_and_extrapolation_on_oracle_counts(monkeypatch):
+    # Sec. III on the oracle's lattice through the same code the GPU scan
+    # uses: each size's Eq. (5) fit agrees with the logistic fit of all its
+    # configurations' critical words within the fit's own (independent-count)
+    # errors, and Eqs. (7)-(8) land in the paper's window
+    stats = pytest.importorskip("scipy.stats")
+    words, _ = _oracle_counts(monkeypatch)
+    sizes = [(W, int(round(W / r))) for W in (8, 12, 16) for r in (2, 1, 0.5, 0.25, 0.125)]
+    curves = fss.scan(sizes, seed=6, n_coarse=256, n_fine=256)
+    pulls = []
+    for (W, L), (f, p, k, n) in curves.items():
+        x = words[(W, L, 6)][: 13 * 256].astype(float) / 2.0**32
+        loc, scale = stats.logistic.fit(x)
+        pulls.append((f.p_c - loc) / f.p_c_err)
+    pulls = np.asarray(pulls)
+    assert np.sqrt(np.mean(pulls ** 2)) < 2.0, pulls
+    fit, law = fss.extrapolate(curves)
+    assert 0.150 < fit.p_inf < 0.162, fit
+    assert -1.30 < law[0][2] < -1.17, law
+
+
+def test_length_statements_on_oracle_counts(monkeypatch):
+    # Sec. III / Fig. 6(a) on the oracle's lattice (reading G13): at p = 0.3 a
+    # W = 6 fibre keeps percolating over W/L >= 1/16, while a W = 3 fibre
+    # loses percolation exponentially with its length, more than ten times
+    # faster
+    _oracle_counts(monkeypatch)
+    six = fss.length_scan(6, [6, 24, 96], [0.3], 1024, 8)[0.3]
+    assert np.all(six[1] / six[2] >= 0.99), six[1]
+    three = fss.length_scan(3, [3, 6, 12, 24, 48, 96], [0.3], 1024, 8)[0.3]
+    assert np.all(np.diff(three[1]) <= 0), three[1]
+    assert three[3].lam > 10 * max(six[3].lam, 1e-6), (three[3], six[3])
