@@ -134,9 +134,10 @@ def measured_peaks():
         return {}
 
 
-def cpu_sample(per_p: int, threads: int, cfg0: int = 0):
+def cpu_sample(per_p: int, threads: int, cfg0: int = 0, results: list | None = None):
     """Time the oracle (Markov mode, as it stands) on per_p configurations at
-    each p of the sweep; returns (site_updates, seconds)."""
+    each p of the sweep; returns (site_updates, seconds).  ``results``, if
+    given, receives the oracle's outputs per p."""
     import oracle
     oracle.build()
     su, t = 0, 0.0
@@ -146,7 +147,26 @@ def cpu_sample(per_p: int, threads: int, cfg0: int = 0):
                            threads=threads)
         t += time.perf_counter() - t0
         su += site_updates(A_COLS, L, r["verdict"], r["first_hit"], r["m_stop"])
+        if results is not None:
+            results.append(r)
     return su, t
+
+
+def sample_parity(pc, refs, per_p: int) -> dict:
+    """The CUDA path's outputs on the oracle's sample (configurations
+    0..per_p-1 at each p, host outputs, outside every timed region):
+    verdicts, first_hit and m_stop must be equal, mass within 1e-5."""
+    bad, err, n_gpu, n_ref = 0, 0.0, 0, 0
+    for p, r in zip(PS, refs):
+        g = pc.pc_inspect(W, L, p, SEED, 0, per_p)
+        same = ((g["verdict"].astype(np.int32) == r["verdict"]) & (g["first_hit"] == r["first_hit"])
+                & (g["m_stop"] == r["m_stop"]))
+        bad += int((~same).sum())
+        err = max(err, float(np.abs(g["mass"].astype(np.float64) - r["mass"]).max()))
+        n_gpu += int(g["n_percolating"]); n_ref += int(r["verdict"].sum())
+    return {"configs": per_p * len(PS), "mismatched_configs": bad, "mass_max_abs_err": err,
+            "mass_tolerance": 1e-5, "percolating": [n_gpu, n_ref],
+            "ok": bad == 0 and err <= 1e-5 and n_gpu == n_ref}
 
 
 def run_reference(args):
@@ -624,10 +644,17 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        su, t = cpu_sample(args.cpu_per_p, threads)
+        refs = []
+        su, t = cpu_sample(args.cpu_per_p, threads, results=refs)
         line["cpu_baseline"] = {"value": su / t, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{args.cpu_per_p} configurations per p x 21 p, "
+                                "sample": f"{args.cpu_per_p} configurations per p x {len(PS)} p, "
                                           f"Markov mode (FP64 CSR), {t:.1f} s"}
+        # verdict and Pi parity on the same sample (first configurations of
+        # the timed workload)
+        try:
+            line["parity"] = sample_parity(pc, refs, args.cpu_per_p)
+        except Exception as e:  # reported in the line, never silently dropped
+            line["parity"] = {"ok": False, "error": repr(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -38,3 +38,34 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not r.stdout.strip()
+
+
+def test_sample_parity_block_flags_any_difference():
+    # the psweep line's "parity" block: the CUDA outputs on the oracle's own
+    # sample; a planted difference in one configuration must be reported
+    import importlib
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module("bench")
+    refs = []
+    bench.cpu_sample(4, 2, results=refs)
+    by_p = dict(zip(bench.PS, refs))
+
+    class Fake:
+        plant = None
+
+        def pc_inspect(self, W, L, p, seed, b, n):
+            r = by_p[p]
+            out = {"verdict": r["verdict"].astype(np.uint8), "first_hit": r["first_hit"].copy(),
+                   "m_stop": r["m_stop"].copy(), "mass": r["mass"].astype(np.float32),
+                   "n_percolating": int(r["verdict"].sum())}
+            if self.plant == p:
+                out["m_stop"][0] += 1
+            return out
+
+    f = Fake()
+    ok = bench.sample_parity(f, refs, 4)
+    assert ok["ok"] and ok["mismatched_configs"] == 0 and ok["configs"] == 4 * len(bench.PS)
+    f.plant = bench.PS[7]
+    bad = bench.sample_parity(f, refs, 4)
+    assert not bad["ok"] and bad["mismatched_configs"] == 1
