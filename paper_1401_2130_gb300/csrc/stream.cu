@@ -49,7 +49,8 @@ constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
 constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
 constexpr int kRowsFP = 128;  // layers per FP unit (the ring prologue is paid once per unit)
 constexpr int kMaxRing = 6;  // ring slots: planes in flight ahead of the compute (deeper rings cost L1)
-// shared memory the ring may take per CTA (two sweep CTAs per SM)
+// shared memory the ring may take per CTA: at least two sweep CTAs fit on an
+// SM (at W = 64 six slots take 39.4 KB, and three CTAs fit)
 constexpr int kRingBudget = 104 * 1024;
 constexpr int kMaxSlots = 4096;
 
