@@ -30,6 +30,7 @@
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -39,42 +40,6 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kResStreams = 4;
-
-// First-fit allocator over [0, size) of one device allocation.
-struct Arena {
-  char* base = nullptr;
-  size_t size = 0;
-  std::map<size_t, size_t> free_;  // offset -> length
-  void init(char* b, size_t n) { base = b; size = n; free_.clear(); free_[0] = n; }
-  bool alloc(size_t n, size_t* off) {
-    n = (n + 255) & ~(size_t)255;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n, o = it->first + n;
-        free_.erase(it);
-        if (rest) free_[o] = rest;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    n = (n + 255) & ~(size_t)255;
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
-    }
-  }
-  size_t largest() const {
-    size_t m = 0;
-    for (auto& kv : free_) m = std::max(m, kv.second);
-    return m;
-  }
-};
 
 enum TicketState { T_PENDING, T_RUNNING, T_DONE, T_FAILED, T_CANCELLED };
 
