@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tune_file.h"
 
 namespace pc {
 
@@ -39,7 +40,7 @@ namespace {
 constexpr double kTunePBins = 40.0;  // p bins of width 0.025
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune;
+std::map<TuneKey, int> g_tune;
 bool g_tune_loaded = false;
 
 int p_bin(double p) { return (int)std::lround(p * kTunePBins); }
@@ -51,13 +52,7 @@ void tune_load() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  // format: {"W,L,pbin": T, ...}
-  int W, L, B, T;
-  int ch;
-  while ((ch = std::fgetc(f)) != EOF) {
-    if (ch != '"') continue;
-    if (std::fscanf(f, "%d,%d,%d\": %d", &W, &L, &B, &T) == 4 && T > 0) g_tune[{W, L, B}] = T;
-  }
+  tune_read(f, kResidentMaxThreads, g_tune);
   std::fclose(f);
 }
 
@@ -67,14 +62,7 @@ void tune_save() {
   const std::string tmp = std::string(path) + ".tmp";
   FILE* f = std::fopen(tmp.c_str(), "w");
   if (!f) return;
-  std::fputs("{", f);
-  bool first = true;
-  for (auto& kv : g_tune) {
-    std::fprintf(f, "%s\"%d,%d,%d\": %d", first ? "" : ", ", std::get<0>(kv.first), std::get<1>(kv.first),
-                 std::get<2>(kv.first), kv.second);
-    first = false;
-  }
-  std::fputs("}\n", f);
+  tune_write(f, g_tune);
   std::fclose(f);
   std::rename(tmp.c_str(), path);
 }

@@ -31,6 +31,7 @@ struct ResidentArgs {
   int prep_chunk;            // layers prepared per lazy chunk (>= 3)
   int bits_only = 0;         // reached set only: no FP32 sweep, mass written 0
 };
+constexpr int kResidentMaxThreads = 640;  // resident CTA size limit: 20 warps at <= 96 registers
 size_t resident_smem(const Lattice& lat);
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st);
 pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g,

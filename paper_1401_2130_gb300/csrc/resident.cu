@@ -42,7 +42,7 @@ namespace pc {
 namespace {
 
 constexpr uint32_t kGrow = 1u, kEnd = 2u;
-constexpr int kMaxThreads = 640;  // 20 warps at <= 96 registers
+constexpr int kMaxThreads = kResidentMaxThreads;
 
 struct Smem {
   float* nu[2];
