@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "plan.h"
 #include "tiling.cuh"
 #include "tma.cuh"
 
@@ -43,8 +44,6 @@ namespace pc {
 namespace {
 
 constexpr uint32_t kGrow = 1u, kEnd = 2u;
-enum : int { PH_EMPTY = 0, PH_DRAW0 = 1, PH_PREP0 = 2, PH_STEP = 3 };
-enum : int { U_FP = 0, U_BITS = 1, U_PREP = 2, U_DRAW = 3, U_CLEAN = 4, U_KINDS = 5 };
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
 constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
 constexpr int kRowsFP = 128;  // layers per FP unit (the ring prologue is paid once per unit)
@@ -114,42 +113,6 @@ struct Ctx {
   unsigned long long* qdone;    // [nq] finished configurations (server mode)
 };
 
-struct Plan {
-  int lo[U_KINDS], hi[U_KINDS];
-  int G2, F2;
-};
-
-__host__ __device__ inline Plan make_plan(int phase, int m, int G, int F, int L, int TW) {
-  Plan p;
-  for (int k = 0; k < U_KINDS; ++k) { p.lo[k] = 0; p.hi[k] = 0; }
-  p.G2 = G; p.F2 = F;
-  if (phase == PH_DRAW0) {
-    const int rows = TW < 2 ? TW : 2;  // first 64 layers
-    p.hi[U_DRAW] = rows;
-    p.G2 = rows * 32 < L ? rows * 32 : L;
-    // a slot may have held another lattice: zero the padding rows and the
-    // sentinel column of this one (one unit per column chunk)
-    p.hi[U_CLEAN] = 1;
-  } else if (phase == PH_PREP0) {
-    p.hi[U_PREP] = L < 5 ? L : 5;
-    p.F2 = p.hi[U_PREP];
-  } else if (phase == PH_STEP) {
-    const int tmax = m < L - 1 ? m : L - 1;
-    p.hi[U_FP] = tmax + 1;
-    p.hi[U_BITS] = (tmax >> 5) + 1;
-    // two layers prepared per tick (the window grows by one); the degrees of
-    // layer F2 - 1 need the occupancy of layer F2: G >= min(F2 + 1, L)
-    int F2 = F + 2 < L ? F + 2 : L;
-    if (G < (F2 + 1 < L ? F2 + 1 : L)) F2 = F;
-    p.lo[U_PREP] = F; p.hi[U_PREP] = F2;
-    p.F2 = F2;
-    if (G < L && G < F2 + 33) {  // keep occupancy a word row ahead
-      p.lo[U_DRAW] = G >> 5; p.hi[U_DRAW] = (G >> 5) + 1;
-      p.G2 = G + 32 < L ? G + 32 : L;
-    }
-  }
-  return p;
-}
 
 // items along the plane / column axis of one unit row, per kind: strips for
 // FP, plane positions for PREP and CLEAN, columns for BITS and DRAW

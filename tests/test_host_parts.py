@@ -1,6 +1,7 @@
-"""Host-only parts of the library, compiled with the host C++ compiler (no
+"""Host-side parts of the library, compiled with the host C++ compiler (no
 GPU): the server's HBM admission allocator (csrc/arena.h) against a granule
-model, and the autotuner's file format (csrc/tune_file.h)."""
+model, the autotuner's file format (csrc/tune_file.h), and the streamed
+solver's tick planner (csrc/plan.h) simulated over many fibre lengths."""
 from __future__ import annotations
 
 import os
@@ -38,3 +39,9 @@ def test_tune_file_round_trip_and_damaged_entries(tmp_path_factory, tmp_path):
     exe = _compile(tmp_path_factory, "tune_file_check")
     r = subprocess.run([exe, str(tmp_path / "tune.json")], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_tick_planner_keeps_every_read_ready(tmp_path_factory):
+    exe = _compile(tmp_path_factory, "plan_check")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout[-3000:] + r.stderr
