@@ -16,6 +16,12 @@ Every function names the passage of the paper it follows:
   on to N_max after the reached set stops growing), 'bfs', 'unionfind'
 * ``first_passage``      -- Appendix Eq. (A.3): forward and backward forms
 * ``first_passage_dense``-- Eq. (3) on an explicit matrix (Fig. 2)
+* ``first_passage_lazy`` -- the self-loop remark of Sec. II.B: the lazy chain
+  hold * I + (1 - hold) * P
+* ``site_words`` / ``occupancy_fixed`` -- Sec. II.A: the fixed-count sample
+  space (the Np smallest keys (word, site))
+* ``critical_words``     -- Sec. II.B spanning path with coupled draws: the
+  word below which each configuration percolates, i.e. its verdict at every p
 """
 from __future__ import annotations
 
