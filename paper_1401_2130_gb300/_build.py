@@ -7,6 +7,7 @@ the library exposes a plain C ABI (include/percol.h).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -44,8 +45,18 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    # one build at a time (the ranks of a multi-GPU run share this tree): the
+    # others wait, then find the library fresh
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build_locked(verbose, ptxas_info)
+
+
+def _build_locked(verbose: bool, ptxas_info: bool) -> str:
+    nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src: str) -> tuple[str, str]:
