@@ -239,6 +239,10 @@ pc_status pc_server_submit(pc_server* s, const pc_query* q, uint64_t* ticket);
  * Wait up to timeout_ns (0: do not wait) for a ticket.  PC_OK fills out and
  * retires the ticket; PC_ERR_BUSY if it is not finished yet (poll again);
  * PC_ERR_CANCELLED if it was cancelled; PC_ERR_ARG for an unknown ticket.
+ * A query whose work failed returns that failure (e.g. PC_ERR_CUDA,
+ * PC_ERR_TIMEOUT, PC_ERR_INTERNAL) and retires the ticket.  If the device
+ * loop itself fails, every queued and running query fails with its status
+ * and later submits return PC_ERR_CANCELLED.
  */
 pc_status pc_server_poll(pc_server* s, uint64_t ticket, pc_result* out, int64_t timeout_ns);
 
