@@ -1,19 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 percolation-inspection hot path.
 
-Workload (one "step"): the p-sweep of the Markov inspection -- modified-FCC
-fibre lattice W = 8, L = 64 (A = 217 columns, N = 13,888 sites), p = 0.100 ..
-0.200 in steps of 0.005 (21 values), 10^4 configurations per p from the
-Philox4x32-10 stream with seed 2, one inspection launch per p.  Metric:
-site-updates per second (every step m of the forward recursion that computes
-mu_m sweeps the causal window of min(m+1, L) layers of A sites).
+Default workload (``--workload large``): the HBM-bound single-lattice case --
+modified-FCC fibre lattice W = 64, L = 4096 (A = 12,481 columns, N = 51.1 M
+sites), p in {0.14, 0.1533, 0.17}, 64 configurations per p from the
+Philox4x32-10 stream with seed 4, solved by the streamed solver (FP32 vector,
+exact reached-set bits, bulk-copy-staged plane segments).  One "step" is one
+block of 8 configurations at each of the three p (three inspection calls);
+the steps cycle through the 8 blocks of the 64 configurations.  Metric:
+site-updates per second (every step m of the forward recursion sweeps the
+causal window of min(m+1, L) layers of A sites), roofline against the
+measured HBM copy bandwidth at 8.375 B per site-update.
+
+Other workloads: ``--workload psweep`` (W = 8, L = 64, p = 0.100 .. 0.200, 10^4
+configurations per p, seed 2, the shared-memory resident solver), ``batch``,
+``serving``, ``fss``.
 
 Default arm: libpercol on the GPU.  ``--impl reference``: the CPU oracle
 (explicit FP64 transition matrix, Sec. II.B) on the host cores, each step a
 bounded sample of the same workload.
 
-Multi-GPU (torchrun, one rank per GPU): weak scaling -- rank r inspects
-configurations [r * 10^4, (r + 1) * 10^4) at every p; no data-path collective.
+Multi-GPU (torchrun, one rank per GPU): weak scaling -- rank r inspects its own
+configuration range at every p; no data-path collective.
 """
 from __future__ import annotations
 
@@ -31,11 +39,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# p-sweep workload (resident solver)
 W, L, SEED, N_CFG = 8, 64, 2, 10_000
 PS = [round(0.100 + 0.005 * k, 3) for k in range(21)]
 A_COLS = 3 * W * (W + 1) + 1
-# Shared-memory traffic model of one site update in the resident solver
-# (gather form): 14 neighbour nu reads + 1/deg read + nu write, FP32.
+# large single-lattice workload (streamed solver, HBM bound)
+LW, LL, LSEED = 64, 4096, 4
+LPS = (0.14, 0.1533, 0.17)
+LA = 3 * LW * (LW + 1) + 1
+# Shared-memory traffic of one site update in the resident solver's gather
+# form (14 neighbour nu reads + 1/deg read + nu write, FP32): a secondary
+# figure of the p-sweep line.
 SMEM_BYTES_PER_SU = 14 * 4 + 4 + 4
 METRIC = "site-updates/s"
 UNIT = "SU/s"
@@ -170,9 +184,67 @@ def sample_parity(pc, refs, per_p: int) -> dict:
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores (rank 0 only; other ranks
+    exit 0 without work), on the workload the GPU arm runs."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "psweep":
+        return run_reference_psweep(args, world)
+    if args.workload != "large":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no oracle timing for --workload {args.workload}; it has none on the default line"}))
+        return 0
+    return run_reference_large(args, world)
+
+
+def markov_sample_large(p: float, cfg0: int, n: int, threads: int):
+    """The oracle's Markov mode on n configurations of the large lattice at p
+    (one configuration per thread); returns (outputs, site_updates, seconds)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.inspect(LW, LL, p=p, seed=LSEED, cfg0=cfg0, n=n, mode="markov", threads=threads)
+    dt = time.perf_counter() - t0
+    return r, site_updates(LA, LL, r["verdict"], r["first_hit"], r["m_stop"]), dt
+
+
+def run_reference_large(args, world):
+    """Each timed step: the oracle's Markov mode (explicit FP64 CSR over the
+    whole lattice, every step) on ``--ref-configs`` configurations at
+    p = 0.14, one per core.  At 51 M sites a p = 0.1533 configuration takes
+    ~45 s in this mode and a p = 0.17 one (about 12,000 steps) on the order
+    of half an hour, so the bounded sample is the low-p one."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n_ref = args.ref_configs or threads
+    p0 = LPS[0]
+    oracle.build()
+    for w in range(args.warmup):  # warm-up: one BFS inspection (page cache, allocator)
+        oracle.inspect(LW, LL, p=p0, seed=LSEED, cfg0=1_000_000 + w, n=1, mode="bfs", threads=1)
+    su_tot, t_tot = 0, 0.0
+    for k in range(args.steps):
+        _, su, dt = markov_sample_large(p0, k * n_ref, n_ref, threads)
+        su_tot += su; t_tot += dt
+    value = su_tot / t_tot
+    sample = (f"Markov mode on {n_ref} configurations per step at p = {p0} (configurations "
+              f"0..{args.steps * n_ref - 1}), one per core")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "large W=64 L=4096 p=0.14/0.1533/0.17 x 64 configs seed=4",
+                   "W": LW, "L": LL, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_psweep(args, world):
     threads = os.cpu_count() or 1
     per_p = args.ref_per_p
     for _ in range(args.warmup):
@@ -216,72 +288,188 @@ def batching_specs(n=10_000):
     return [(Wb, Wb * r, 0.1533, 3, 0, n) for Wb in (4, 8, 16, 32) for r in (1, 2, 4, 8, 16, 32, 64)]
 
 
-def run_large(args, pc, torch):
+def solve_ticks(verdict, first_hit, m_stop) -> int:
+    """Ticks of one streamed solve whose configurations all hold a slot at
+    once: the draw and preparation ticks, then one tick per step of the
+    longest configuration."""
+    steps = np.where(np.asarray(verdict) != 0, np.asarray(first_hit) - 1, np.asarray(m_stop))
+    return int(steps.max(initial=0)) + 3
+
+
+def run_large(args, pc, torch, rank, world, local, dist):
     """W = 64, L = 4096 (51.1 M sites), p in {0.14, 0.1533, 0.17}, 64
-    configurations each, seed 4: the streamed solver, HBM bound."""
-    Wl, Ll, seed, n = 64, 4096, 4, args.large_configs
-    ps = [0.14, 0.1533, 0.17] if args.large_p is None else [float(v) for v in args.large_p.split(",")]
-    A = 3 * Wl * (Wl + 1) + 1
+    configurations each, seed 4: the streamed solver, HBM bound.  One step =
+    one block of configurations at each p; steps cycle through the blocks."""
+    ps = list(LPS) if args.large_p is None else [float(v) for v in args.large_p.split(",")]
+    n = args.large_configs
+    block = max(1, min(args.large_block, n))
+    nb = max(1, n // block)
+    base = rank * n  # weak scaling: rank r owns configurations [r n, (r + 1) n) at every p
     stream = torch.cuda.current_stream()
-    outs = [pc._alloc_outputs(n, True, pc.ALL_OUTPUTS) for _ in ps]
-    for _ in range(args.warmup):  # warm-up on one configuration per p
+    outs = {p: pc._alloc_outputs(nb * block, True, pc.ALL_OUTPUTS) for p in ps}
+    nperc = torch.zeros((nb, len(ps)), dtype=torch.int64, device="cuda")
+
+    def block_out(i, p, b):
+        o, sl = outs[p], slice(b * block, (b + 1) * block)
+        return {"verdict": o["verdict"][sl], "first_hit": o["first_hit"][sl], "mass": o["mass"][sl],
+                "m_stop": o["m_stop"][sl], "n_percolating": nperc[b, i:i + 1]}
+
+    def step(b):
+        for i, p in enumerate(ps):
+            pc.pc_inspect(LW, LL, p, LSEED, base + b * block, block, device=True, out=block_out(i, p, b),
+                          stream=stream, bits_only=args.bits_only)
+
+    # warm-up: one configuration per p, outside the timed configuration range
+    wo = pc._alloc_outputs(1, True, pc.ALL_OUTPUTS)
+    for w in range(args.warmup):
         for p in ps:
-            pc.pc_inspect(Wl, Ll, p, seed, 0, 1, device=True, stream=stream, bits_only=args.bits_only)
+            pc.pc_inspect(LW, LL, p, LSEED, base + nb * block + w, 1, device=True, out=wo, stream=stream,
+                          bits_only=args.bits_only)
     torch.cuda.synchronize()
-    times = []
-    with Clocks(0) as clk:
-        for _ in range(args.steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            ev[0].record(stream)
-            for i, p in enumerate(ps):
-                pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=True, out=outs[i], stream=stream,
-                              bits_only=args.bits_only)
-            ev[1].record(stream)
+    times, blocks = [], []
+    with Clocks(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            b = k % nb
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(b)
+            e1.record(stream)
             torch.cuda.synchronize()
-            times.append(ev[0].elapsed_time(ev[1]) / 1e3)
-    su = 0
-    perc = []
-    ticks = 0
-    for o in outs:
-        h = {k: v.cpu().numpy() for k, v in o.items()}
-        su += site_updates(A, Ll, h["verdict"], h["first_hit"], h["m_stop"])
-        perc.append(int(h["verdict"].sum()))
-        steps = np.where(h["verdict"] != 0, h["first_hit"] - 1, h["m_stop"])
-        # one wave of slots: draw + prepare ticks, then one tick per step
-        ticks += int(steps.max(initial=0)) + 3
-    t = float(np.mean(times))
+            times.append(e0.elapsed_time(e1) / 1e3)
+            blocks.append(b)
+        if dist is not None:
+            dist.barrier()
+        wall = time.perf_counter() - t_wall
+    host = {p: {k: v.cpu().numpy() for k, v in outs[p].items()} for p in ps}
+
+    def block_su(b):
+        sl = slice(b * block, (b + 1) * block)
+        return sum(site_updates(LA, LL, host[p]["verdict"][sl], host[p]["first_hit"][sl],
+                                host[p]["m_stop"][sl]) for p in ps)
+
+    def block_ticks(b):
+        sl = slice(b * block, (b + 1) * block)
+        return sum(solve_ticks(host[p]["verdict"][sl], host[p]["first_hit"][sl], host[p]["m_stop"][sl])
+                   for p in ps)
+
+    su_rank = sum(block_su(b) for b in blocks)
+    t_rank = float(sum(times))
+    su_all, t_max = su_rank, t_rank
+    if dist is not None:
+        tt = torch.tensor([t_rank], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        st_ = torch.tensor([float(su_rank)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(st_, op=dist.ReduceOp.SUM)
+        su_all = int(st_.item())
+    value = su_all / t_max
+
     # end to end through the public call with host outputs (D2H inside)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for p in ps:
-        pc.pc_inspect(Wl, Ll, p, seed, 0, n, device=False, bits_only=args.bits_only)
+    su_e2e = 0
+    for k in range(e2e_steps):
+        b = k % nb
+        for p in ps:
+            r = pc.pc_inspect(LW, LL, p, LSEED, base + b * block, block, bits_only=args.bits_only)
+            su_e2e += site_updates(LA, LL, r["verdict"], r["first_hit"], r["m_stop"])
     e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+        st_ = torch.tensor([float(su_e2e)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(st_, op=dist.ReduceOp.SUM)
+        su_e2e = int(st_.item())
+
     peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm = peaks.get("hbm_gbs") or 6800.0
     bps = BITS_BYTES_PER_SU if args.bits_only else HBM_BYTES_PER_SU
-    achieved = bps * su / t / 1e9
-    return {
-        "metric": METRIC, "value": su / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    # per step of this rank (the unit the events time): algorithmic bytes / time
+    achieved = bps * su_rank / t_rank / 1e9
+    traffic = None
+    if not args.bits_only and SWEEP_DRAM_BYTES_PER_SU is not None:
+        traffic = SWEEP_DRAM_BYTES_PER_SU * su_rank / len(times)
+    perc = {str(p): int(host[p]["verdict"][:len(set(blocks)) * block].sum()) for p in ps}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"large W=64 L=4096 p={'/'.join(str(p) for p in ps)} x {n} configs seed=4"
                                + (" (bits only)" if args.bits_only else ""),
-                   "site_updates_per_step": su, "percolating_per_p": perc, "solver": "streamed",
-                   "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB)"},
-        "configs_per_s": n * len(ps) / t,
+                   "W": LW, "L": LL, "configs_per_p": n, "configs_per_step": block * len(ps) * world,
+                   "step": f"configurations [{block}b, {block}b + {block}) at each p, b = step mod {nb}",
+                   "site_updates_per_step": su_all / len(times), "percolating_per_p": perc,
+                   "solver": "streamed", "parallelism": f"configs sharded over {world} GPU(s)",
+                   "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB), no flush"},
+        "configs_per_s": block * len(ps) * world * len(times) / t_max,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm,
-                     "traffic": None if args.bits_only else SWEEP_DRAM_BYTES_PER_SU * su,
-                     "traffic_note": "ncu DRAM bytes per site-update of sweep_kernel (controlled capture, "
-                                     "4 active slots) x the step's site-updates",
-                     "model": f"{bps} B/site-update x site-updates / time of the whole "
-                              "solve (sweep + control kernels), peak = measured copy bandwidth"},
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "traffic_note": "ncu DRAM bytes (read + write) per site-update of sweep_kernel "
+                                     "(controlled capture, all slots active) x the step's site-updates",
+                     "model": f"{bps} B/site-update x site-updates of a step / CUDA-event time of the "
+                              "step (every kernel of the solve), peak = measured copy bandwidth "
+                              "(MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clk.summary(),
-        "e2e": {"value": su / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": len(ps) * (n * (1 + 4 + 4 + 4) + 8)},
-        # kernel nodes run by the streamed solver's graphs: a sweep and a
-        # control kernel per tick, plus the query upload and init kernels
-        "gpu_launches": 2 * ticks + 2 * len(ps),
+        "e2e": {"value": su_e2e / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": len(ps) * (block * (1 + 4 + 4 + 4) + 8)},
+        # kernels of each solve: query upload and init, then a sweep and a
+        # control kernel per tick
+        "gpu_launches": sum(block_ticks(b) * 2 + 2 * len(ps) for b in blocks),
+        "step_ms": [round(t * 1e3, 3) for t in times],
+        "wall_s_timed": wall,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["parity"] = large_cpu_leg(args, host, ps, block, sorted(set(blocks)))
+    return line
+
+
+def large_cpu_leg(args, host, ps, block, seen):
+    """The oracle on the host cores: Markov mode timed on a bounded sample
+    (cpu_baseline), plus BFS on the first block at every p; both compared with
+    the CUDA path's outputs of the same configurations (parity)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    avail = len(seen) * block if seen == list(range(len(seen))) else block
+    n_m = max(1, min(args.cpu_configs or threads, avail))
+    p0 = ps[0]
+    ref, su_m, tm = markov_sample_large(p0, 0, n_m, threads)
+    t0 = time.perf_counter()
+    bfs = {p: oracle.inspect(LW, LL, p=p, seed=LSEED, cfg0=0, n=block, mode="bfs", threads=threads)
+           for p in ps}
+    tb = time.perf_counter() - t0
+    su_b = sum(site_updates(LA, LL, r["verdict"], r["first_hit"], r["m_stop"]) for r in bfs.values())
+    cpu = {"value": su_m / tm, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"Markov mode (explicit FP64 CSR over the whole lattice every step) on configurations "
+                     f"0..{n_m - 1} at p = {p0}, {tm:.1f} s; the p = 0.1533 and 0.17 configurations take "
+                     f"~45 s and ~30 min each in this mode",
+           "bfs_route": {"configs_per_s": len(ps) * block / tb, "seconds": tb,
+                         "sample": f"configurations 0..{block - 1} at every p",
+                         "note": "breadth-first search: verdict, first_hit and m_stop only, no mass; "
+                                 f"the Markov site-updates of these configurations would be {su_b:.3e}"}}
+    bad, n_cmp, n_gpu, n_ref = 0, 0, 0, 0
+    for p in ps:
+        g, r = host[p], bfs[p]
+        same = ((g["verdict"][:block].astype(np.int32) == r["verdict"]) & (g["first_hit"][:block] == r["first_hit"])
+                & (g["m_stop"][:block] == r["m_stop"]))
+        bad += int((~same).sum()); n_cmp += block
+        n_gpu += int(g["verdict"][:block].sum()); n_ref += int(r["verdict"].sum())
+    g = host[p0]
+    same = ((g["verdict"][:n_m].astype(np.int32) == ref["verdict"]) & (g["first_hit"][:n_m] == ref["first_hit"])
+            & (g["m_stop"][:n_m] == ref["m_stop"]))
+    bad_m = int((~same).sum())
+    err = float(np.abs(g["mass"][:n_m].astype(np.float64) - ref["mass"]).max(initial=0.0))
+    parity = {"configs": n_cmp + n_m, "routes": f"BFS: {n_cmp} configurations (block 0 at every p); "
+                                                f"Markov: {n_m} at p = {p0}",
+              "mismatched_configs": bad + bad_m, "mass_max_abs_err": err, "mass_tolerance": 1e-5,
+              "percolating_bfs_sample": [n_gpu, n_ref],
+              "ok": bad + bad_m == 0 and err <= 1e-5 and n_gpu == n_ref}
+    return cpu, parity
 
 
 def run_batch(args, pc, torch):
@@ -485,55 +673,9 @@ def run_fss(args, pc, torch):
     }
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ref-per-p", type=int, default=1000)
-    ap.add_argument("--cpu-per-p", type=int, default=N_CFG)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--configs-per-p", type=int, default=N_CFG,
-                    help="smaller cases for profiling only; the benchmark workload is 10^4")
-    ap.add_argument("--workload", default="psweep", choices=["psweep", "large", "batch", "serving", "fss"])
-    ap.add_argument("--serve-queries", type=int, default=24)
-    ap.add_argument("--serve-budget-gb", type=int, default=128)
-    ap.add_argument("--large-configs", type=int, default=64)
-    ap.add_argument("--batch-configs", type=int, default=10_000)
-    ap.add_argument("--bits-only", action="store_true",
-                    help="verdicts only (PC_BITS_ONLY): the reached-set propagation without the FP32 recursion")
-    ap.add_argument("--large-p", default=None,
-                    help="comma list of p for the large workload (a profiling subset)")
-    ap.add_argument("--only-p", type=float, default=None,
-                    help="p-sweep at this one p (a profiling subset, not the benchmark workload)")
-    args = ap.parse_args()
-    global PS
-    if args.only_p is not None:
-        PS = [args.only_p]
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload != "psweep":
-        import torch
-        import paper_1401_2130_gb300 as pc
-        torch.cuda.set_device(0)
-        pc.build()
-        pc.load()
-        fn = {"large": run_large, "batch": run_batch, "serving": run_serving, "fss": run_fss}[args.workload]
-        print(json.dumps(fn(args, pc, torch)), flush=True)
-        return 0
-
-    import torch
-    import paper_1401_2130_gb300 as pc
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    pc.build()
-    pc.load()
+def run_psweep(args, pc, torch, rank, world, local, dist):
+    """W = 8, L = 64 p-sweep through the shared-memory resident solver (one
+    launch per p, 10^4 configurations each)."""
     n_cfg = args.configs_per_p
     cfg0, _ = shard_range(rank, n_cfg)
     stream = torch.cuda.current_stream()
@@ -609,7 +751,9 @@ def main():
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
     smem_peak = nsm * 128 * sm_max * 1e6 / 1e9  # GB/s: 32 banks x 4 B per clock per SM
-    achieved = SMEM_BYTES_PER_SU * su_step / (sum(launch_ms) / len(step_ms) / 1e3) / 1e9
+    t_launch = sum(launch_ms) / len(step_ms) / 1e3  # resident launches of one step
+    achieved = HBM_BYTES_PER_SU * su_step / t_launch / 1e9
+    gather = SMEM_BYTES_PER_SU * su_step / t_launch / 1e9
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -628,13 +772,13 @@ def main():
                      "frac": achieved / smem_peak, "traffic": RESIDENT_DRAM_BYTES_PER_LAUNCH,
                      "traffic_note": "HBM bytes per resident_kernel launch (ncu): the state lives in "
                                      "shared memory, HBM carries tables and outputs only",
-                     "model": f"{SMEM_BYTES_PER_SU} B of shared-memory traffic per site update; "
-                              f"peak = {nsm} SMs x 128 B/clk x {sm_max:.0f} MHz (derived)",
-                     # the same throughput under the state-traffic model of
-                     # the streamed solver (8.375 B per site-update)
-                     "state_model": {"bytes_per_su": HBM_BYTES_PER_SU,
-                                     "achieved": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU,
-                                     "frac": achieved * HBM_BYTES_PER_SU / SMEM_BYTES_PER_SU / smem_peak}},
+                     "model": f"{HBM_BYTES_PER_SU} B per site update (nu read and write, occupancy, "
+                              f"reached-set bits) / CUDA-event time of the step's launches; peak = "
+                              f"{nsm} SMs x 128 B/clk x {sm_max:.0f} MHz (derived shared-memory rate)",
+                     # the same throughput under the gather form of Eq. (3):
+                     # 14 neighbour reads, 1/deg and the write, 4 B each
+                     "gather_model": {"bytes_per_su": SMEM_BYTES_PER_SU, "achieved": gather,
+                                      "frac": gather / smem_peak}},
         "clocks": clocks,
         "e2e": {"value": su_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h},
@@ -655,6 +799,67 @@ def main():
             line["parity"] = sample_parity(pc, refs, args.cpu_per_p)
         except Exception as e:  # reported in the line, never silently dropped
             line["parity"] = {"ok": False, "error": repr(e)}
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "psweep", "batch", "serving", "fss"])
+    ap.add_argument("--ref-per-p", type=int, default=1000, help="psweep reference arm: configurations per p")
+    ap.add_argument("--ref-configs", type=int, default=0,
+                    help="large reference arm: Markov configurations per step (0 = one per core)")
+    ap.add_argument("--cpu-per-p", type=int, default=N_CFG)
+    ap.add_argument("--cpu-configs", type=int, default=0,
+                    help="large line's cpu_baseline: Markov configurations (0 = one per core)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs-per-p", type=int, default=N_CFG,
+                    help="smaller cases for profiling only; the benchmark workload is 10^4")
+    ap.add_argument("--serve-queries", type=int, default=24)
+    ap.add_argument("--serve-budget-gb", type=int, default=128)
+    ap.add_argument("--large-configs", type=int, default=64)
+    ap.add_argument("--large-block", type=int, default=8,
+                    help="configurations per p in one step of the large workload")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batch-configs", type=int, default=10_000)
+    ap.add_argument("--bits-only", action="store_true",
+                    help="verdicts only (PC_BITS_ONLY): the reached-set propagation without the FP32 recursion")
+    ap.add_argument("--large-p", default=None,
+                    help="comma list of p for the large workload (a profiling subset)")
+    ap.add_argument("--only-p", type=float, default=None,
+                    help="p-sweep at this one p (a profiling subset, not the benchmark workload)")
+    args = ap.parse_args()
+    global PS
+    if args.only_p is not None:
+        PS = [args.only_p]
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload in ("batch", "serving", "fss"):
+        import torch
+        import paper_1401_2130_gb300 as pc
+        torch.cuda.set_device(0)
+        pc.build()
+        pc.load()
+        fn = {"batch": run_batch, "serving": run_serving, "fss": run_fss}[args.workload]
+        print(json.dumps(fn(args, pc, torch)), flush=True)
+        return 0
+
+    import torch
+    import paper_1401_2130_gb300 as pc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pc.build()
+    pc.load()
+    fn = run_large if args.workload == "large" else run_psweep
+    line = fn(args, pc, torch, rank, world, local, dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

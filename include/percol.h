@@ -185,6 +185,13 @@ typedef struct pc_result {
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
  * applies to every query of the batch; any other flag bit is PC_ERR_ARG.
  * Results equal those of pc_inspect on each query.
+ * Threads: calls from several host threads are safe.  A cached batch is
+ * reference counted, so evicting it (or pc_shutdown) never frees one that a
+ * running call uses.  Replays of the same batch are serialised: each waits,
+ * on its own stream, for the previous replay (of any stream, PC_ASYNC
+ * included) to finish, because they share counters and the output buffers
+ * named in the queries.  A PC_ASYNC batch's outputs are therefore rewritten
+ * by the next submission of the same batch once that one runs.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL.
  */
 #define PC_ASYNC 0x2
@@ -271,8 +278,10 @@ pc_status pc_server_destroy(pc_server* s);
  * Arguments and outputs as pc_inspect with host outputs (all output pointers
  * are HOST pointers; verdicts required, the others optional); the call
  * synchronises cuda_stream before returning.
- * Limits: n_configs <= 262144; W <= 51 (at most 8192 columns); the lattice
- * must fit the resident solver's shared memory.  Anything larger returns
+ * Limits: n_configs <= 262144; W <= 51 (at most 8192 columns, the size of
+ * the static tables); the lattice must fit the resident solver's shared
+ * memory, which on GB300 (227 KB per CTA) bounds it further: W <= 26 (at
+ * L = 1), W = 20 up to L = 8, W = 8 up to L = 80.  Anything larger returns
  * PC_ERR_ARG with a message, before any work is enqueued.
  * Sharing: every call on a device uses the same static array, which keeps
  * the previous call's contents; counters are cleared and tables rewritten on
@@ -280,7 +289,9 @@ pc_status pc_server_destroy(pc_server* s);
  * the array and must be serialised by the caller.
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make it before any
- * stream capture starts.
+ * stream capture starts.  After cudaDeviceReset call pc_shutdown() before
+ * the next call: it forgets the cached address (and every other cached
+ * device object of the library).
  * Errors: PC_ERR_ARG, PC_ERR_CUDA.
  */
 pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t seed,
@@ -322,7 +333,9 @@ pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_
 pc_status pc_lazy_mass(const int32_t* first_hit, const float* mass, int64_t n_configs,
                        double hold, float* mass_lazy, int32_t flags, void* cuda_stream);
 
-/* Release cached lattice tables and scratch of every device. */
+/* Release cached lattice tables, batch graphs and scratch of every device,
+ * and forget the static array's cached device addresses (pc_inspect_static).
+ * Call it after cudaDeviceReset, before any further call of the library. */
 pc_status pc_shutdown(void);
 
 /* Thread-local message of the last failing call ("" if none). */

@@ -278,6 +278,7 @@ pc_status pc_inspect_occupancy(int32_t W, int32_t L, const uint32_t* occ_bits, i
 pc_status pc_shutdown(void) {
   release_batches();
   release_lattices();
+  release_static();
   return PC_OK;
 }
 

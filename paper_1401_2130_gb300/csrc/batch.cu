@@ -17,6 +17,7 @@
 #include <cstring>
 #include <list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -139,10 +140,21 @@ struct BatchGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<QueryPlan> qp;
+  // One replay at a time: a call holds mu from its launch to its last copy,
+  // and every replay first waits (on its own stream) for the event the
+  // previous replay recorded, so replays on different streams never overlap
+  // on the device (they share the counters and the output staging).
+  std::mutex mu;
+  cudaEvent_t done = nullptr;
 };
 
+void destroy_batch(BatchGraph* b);
+// The cache and every running call hold a reference; a batch evicted or
+// released while a call still uses it is destroyed when that call drops it.
+using BatchPtr = std::shared_ptr<BatchGraph>;
+
 std::mutex g_batch_mu;
-std::list<BatchGraph*> g_batches;  // most recent first
+std::list<BatchPtr> g_batches;  // most recent first
 constexpr size_t kMaxCached = 8;
 
 void destroy_batch(BatchGraph* b) {
@@ -151,6 +163,7 @@ void destroy_batch(BatchGraph* b) {
   cudaGetDevice(&cur);
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
+  if (b->done) cudaEventDestroy(b->done);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->plan) stream_plan_release(b->plan, 0);
@@ -179,6 +192,10 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
   b->mem_bytes = bytes;
   cudaError_t e = cudaMalloc((void**)&b->mem, bytes);
   if (e != cudaSuccess) { delete b; return cuda_fail(e, "batch memory"); }
+  if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess) {
+    destroy_batch(b);
+    return cuda_fail(e, "batch event");
+  }
   pc_status rc = PC_OK;
   std::vector<StreamQuery> sq;
   do {
@@ -254,9 +271,12 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
 }  // namespace
 
 void release_batches() {
-  std::lock_guard<std::mutex> lk(g_batch_mu);
-  for (BatchGraph* b : g_batches) destroy_batch(b);
-  g_batches.clear();
+  std::list<BatchPtr> drop;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    drop.swap(g_batches);
+  }
+  // destroyed here, or by the last call still using one
 }
 
 }  // namespace pc
@@ -285,26 +305,36 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
   int dev = 0;
   PC_CUDA(cudaGetDevice(&dev));
   const std::string key = batch_key(q, nq, flags, dev);
-  BatchGraph* b = nullptr;
+  BatchPtr b;
   {
     std::lock_guard<std::mutex> lk(g_batch_mu);
     for (auto it = g_batches.begin(); it != g_batches.end(); ++it)
       if ((*it)->key == key) { b = *it; g_batches.erase(it); g_batches.push_front(b); break; }
   }
   if (!b) {
-    pc_status rc = build_batch(q, nq, flags, st, &b);
+    BatchGraph* raw = nullptr;
+    pc_status rc = build_batch(q, nq, flags, st, &raw);
     if (rc) return rc;
-    b->key = key;
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    g_batches.push_front(b);
-    while (g_batches.size() > kMaxCached) { destroy_batch(g_batches.back()); g_batches.pop_back(); }
+    raw->key = key;
+    b = BatchPtr(raw, destroy_batch);
+    std::list<BatchPtr> evicted;
+    {
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      g_batches.push_front(b);
+      while (g_batches.size() > kMaxCached) { evicted.push_back(g_batches.back()); g_batches.pop_back(); }
+    }
   }
+  std::lock_guard<std::mutex> replay(b->mu);
+  PC_CUDA(cudaStreamWaitEvent(st, b->done, 0));
   PC_CUDA(cudaGraphLaunch(b->exec, st));
   if (dev_out)
     for (int64_t i = 0; i < nq; ++i)
       if (q[i].n_percolating)
         PC_CUDA(cudaMemcpyAsync(q[i].n_percolating, b->qp[i].n_perc, 8, cudaMemcpyDeviceToDevice, st));
-  if (async) return PC_OK;
+  if (async) {
+    PC_CUDA(cudaEventRecord(b->done, st));
+    return PC_OK;
+  }
   int err = 0;
   if (b->plan) PC_CUDA(cudaMemcpyAsync(&err, stream_plan_error(b->plan), sizeof(int), cudaMemcpyDeviceToHost, st));
   std::vector<unsigned long long> cnt((size_t)nq);
@@ -319,6 +349,7 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
       if (q[i].m_stop) PC_CUDA(cudaMemcpyAsync(q[i].m_stop, P.ms, 4 * n, cudaMemcpyDeviceToHost, st));
     }
   }
+  PC_CUDA(cudaEventRecord(b->done, st));
   PC_CUDA(cudaStreamSynchronize(st));
   if (err & 2) { set_error("streamed solver: a bulk-copy wait timed out"); return PC_ERR_TIMEOUT; }
   if (err) { set_error("streamed solver: tick bound or segment check failed"); return PC_ERR_INTERNAL; }

@@ -43,6 +43,7 @@ int resident_threads(int A, int L);
 int tuned_threads(const Lattice& lat, double p, uint64_t seed, cudaStream_t st);
 bool resident_fits(int W, int L);
 void release_batches();
+void release_static();  // noalloc.cu: forget the static array's cached addresses
 
 // Streamed solver for lattices beyond shared memory, stream.cu.
 struct StreamQuery {

@@ -24,7 +24,15 @@
 //
 // Set-up: the first call on a device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current, and caches it.
-// Make that first call before any stream capture begins.
+// Make that first call before any stream capture begins.  A device reset
+// (cudaDeviceReset) invalidates the cached address; pc_shutdown() forgets it
+// (with every other cached device object), and the next call looks it up
+// again.
+//
+// Limits in practice: the resident solver holds the whole configuration in
+// one CTA's shared memory (227 KB on GB300), which bounds the lattice long
+// before the tables do: W <= 26 (at L = 1), W = 20 up to L = 8, W = 8 up to
+// L = 80.
 #include <mutex>
 
 #include "common.cuh"
@@ -112,6 +120,12 @@ __global__ void static_tables_kernel(int W, int A, int32_t* nbr, int8_t* sigma) 
 
 }  // namespace
 
+// Forget the cached device addresses of the static array (pc_shutdown).
+void release_static() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int d = 0; d < kMaxDevices; ++d) g_addr[d] = nullptr;
+}
+
 }  // namespace pc
 
 using namespace pc;
@@ -139,6 +153,13 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
     set_error("pc_inspect_static: lattice state exceeds one CTA's shared memory"); return PC_ERR_ARG;
   }
   if (n_configs > 0 && !verdicts) { set_error("pc_inspect_static: verdicts must not be NULL"); return PC_ERR_ARG; }
+  // the layout's sizes are checked against the static tables before any
+  // work is enqueued
+  int P = 0, s_begin = 0, n_strips = 0;
+  layout_fill(W, &P, &s_begin, &n_strips, nullptr, nullptr, nullptr, nullptr);
+  if (P > kStaticMaxP || n_strips > kStaticMaxStrips) {
+    set_error("pc_inspect_static: layout exceeds the static tables"); return PC_ERR_ARG;
+  }
   unsigned char* base = nullptr;
   pc_status rc = static_scratch(&base);
   if (rc) return rc;
@@ -166,14 +187,9 @@ extern "C" pc_status pc_inspect_static(int32_t W, int32_t L, double p, uint64_t 
   PC_CUDA(cudaMemsetAsync(base, 0, kCtrBytes, st));
   static_tables_kernel<<<(A + 127) / 128, 128, 0, st>>>(W, A, nbr, sig);
   PC_CUDA(cudaGetLastError());
-  int P = 0, s_begin = 0, n_strips = 0;
   {
     // pageable copies from static host tables: they synchronise, but allocate nothing
     std::lock_guard<std::mutex> lk(g_host_mu);
-    layout_fill(W, &P, &s_begin, &n_strips, nullptr, nullptr, nullptr, nullptr);
-    if (P > kStaticMaxP || n_strips > kStaticMaxStrips) {
-      set_error("pc_inspect_static: layout exceeds the static tables"); return PC_ERR_ARG;
-    }
     layout_fill(W, nullptr, nullptr, nullptr, h_srow, h_roff, h_ppos, h_pcol);
     PC_CUDA(cudaMemcpyAsync(d_ppos, h_ppos, sizeof(int32_t) * A, cudaMemcpyHostToDevice, st));
     PC_CUDA(cudaMemcpyAsync(d_pcol, h_pcol, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));

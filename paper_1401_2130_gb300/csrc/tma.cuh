@@ -1,13 +1,22 @@
 // tma.cuh -- bulk asynchronous copies (TMA, cp.async.bulk) and mbarriers in
-// inline PTX for sm_103a.  Every wait is bounded: after kWaitLimit failed
-// polls it reports a timeout instead of spinning on.
+// inline PTX for sm_103a.  Every wait is bounded in time: once kWaitNs of
+// the global nanosecond timer have passed without the phase completing it
+// reports a timeout instead of spinning on.
 #pragma once
 
 #include <stdint.h>
 
 namespace pc {
 
-constexpr unsigned kWaitLimit = 1u << 24;
+// 1 s: a bulk copy of a few KB lands in microseconds, so only a broken copy
+// (or a device stalled by a fault elsewhere) ever reaches it
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -52,11 +61,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false once kWaitNs have
+// passed (the timer is read only when the first poll fails).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned i = 0; i < kWaitLimit; ++i)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
 }
 
 }  // namespace pc

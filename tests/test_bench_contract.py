@@ -13,9 +13,33 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _run(extra_env=None, *args):
     env = dict(os.environ, **(extra_env or {}))
+    args = args or ("--workload", "psweep", "--ref-per-p", "5")
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--steps", "1", "--warmup", "0", "--ref-per-p", "5", *args],
+                           "--steps", "1", "--warmup", "0", *args],
                           capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+
+
+def _check_line(r):
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+              "cpu_baseline", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == "site-updates/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    return d
+
+
+def test_reference_arm_large_workload_line():
+    """The default workload's reference arm: the oracle's Markov mode on the
+    W = 64, L = 4096 lattice, one configuration per step here."""
+    d = _check_line(_run(None, "--ref-configs", "1"))
+    assert "W=64 L=4096" in d["config"]["workload"]
 
 
 def test_reference_arm_prints_one_contract_line():

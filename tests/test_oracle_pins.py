@@ -262,6 +262,30 @@ def test_single_tube_wide_fibre(L):
             assert r["m_stop"][c] == k
 
 
+@pytest.mark.parametrize("W,L,seed,spread", [(3, 12, 5, None), (8, 30, 6, None), (16, 40, 7, 6)])
+def test_wire_first_passage_closed_form(W, L, seed, spread):
+    """A single induced path of metallic sites from t = 0 to t = L-1 (the
+    parity tests' wires): the walk can only follow it, so the first hit is at
+    m = number of path sites and the absorbed mass is 2^-(sites-1) exactly
+    (deg 1 at the start, 2 inside, 2 at the end with the detector edge).
+    The path is built from the geometric contact table, and verified here to
+    be induced by BFS of the oracle itself."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import _wires
+    occ, sites = _wires.wire_occupancies(W, L, 6, seed, spread=spread)
+    nbr, cnt = oracle.adjacency(W, L)
+    for c in range(occ.shape[0]):
+        on = np.flatnonzero(occ[c])
+        # every wire site has at most 2 metallic contacts (induced path)
+        deg = [int(sum(occ[c][j] for j in nbr[i, :cnt[i]])) for i in on]
+        assert max(deg) <= 2 and sorted(deg).count(1) == (2 if len(on) > 1 else 0)
+    r = oracle.inspect(W, L, occ=occ, mode="markov")
+    b = oracle.inspect(W, L, occ=occ, mode="bfs")
+    assert np.array_equal(r["first_hit"], sites) and np.array_equal(b["first_hit"], sites)
+    assert np.array_equal(r["mass"], 2.0 ** -(sites - 1.0))
+
+
 def _all_patterns(N):
     k = np.arange(2**N, dtype=np.uint32)
     return ((k[:, None] >> np.arange(N, dtype=np.uint32)) & 1).astype(np.uint8)

@@ -12,10 +12,12 @@ tests in a run that stops at the first failure.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_1401_2130_gb300 as pc
 
 pytestmark = pytest.mark.gpu
@@ -70,3 +72,31 @@ def test_static_entry_point_rejects_oversized_requests():
                                    None, None, None)
         assert st == pc.PC_ERR_ARG
         assert lib.pc_last_error()
+
+
+@pytest.mark.parametrize("W,L,p,n", [
+    (26, 1, 0.5, 400),    # the widest lattice the resident solver holds
+    (20, 8, 0.3, 300),    # W = 20: its longest resident fibre
+    (12, 40, 0.2, 300),
+    (8, 80, 0.21, 400),   # W = 8: its longest resident fibre
+])
+def test_static_entry_point_matches_the_oracle(W, L, p, n):
+    """The static tables are built on the device by their own kernel, so they
+    are checked against the CPU oracle directly: verdicts, first hits and
+    step counts exact, FP32 mass within 1e-5 absolute and, where the FP64
+    mass exceeds 1e-30, within the relative bound of the parity tests
+    ((3 + 7 (first_hit - 1) + ceil(P / 32) + 10) 2^-24, times 1.01)."""
+    got = _call_static(W, L, p, 17, 0, n)
+    ref = oracle.inspect(W, L, p=p, seed=17, n=n, mode="markov", threads=os.cpu_count() or 1)
+    assert np.array_equal(got["verdict"].astype(np.int32), ref["verdict"])
+    assert np.array_equal(got["first_hit"], ref["first_hit"])
+    assert np.array_equal(got["m_stop"], ref["m_stop"])
+    mg, mr = got["mass"].astype(np.float64), ref["mass"]
+    assert np.abs(mg - mr).max() <= MASS_TOL
+    sel = mr > 1e-30
+    P = pc.pc_lattice_layout(W)["P"]
+    fh = np.maximum(ref["first_hit"][sel], 1)
+    tol = 1.01 * (3 + 7 * (fh - 1) + (P + 31) // 32 + 10) * 2.0 ** -24
+    assert np.all(np.abs(mg[sel] - mr[sel]) <= tol * mr[sel])
+    assert got["n_percolating"] == int(ref["verdict"].sum())
+    assert ref["verdict"].sum() > 0
