@@ -281,7 +281,7 @@ pc_status pc_server_destroy(pc_server* s);
  * Limits: n_configs <= 262144; W <= 51 (at most 8192 columns, the size of
  * the static tables); the lattice must fit the resident solver's shared
  * memory, which on GB300 (227 KB per CTA) bounds it further: W <= 26 (at
- * L = 1), W = 20 up to L = 8, W = 8 up to L = 80.  Anything larger returns
+ * L = 1), W = 20 up to L = 8, W = 8 up to L = 74.  Anything larger returns
  * PC_ERR_ARG with a message, before any work is enqueued.
  * Sharing: every call on a device uses the same static array, which keeps
  * the previous call's contents; counters are cleared and tables rewritten on

@@ -32,7 +32,7 @@
 // Limits in practice: the resident solver holds the whole configuration in
 // one CTA's shared memory (227 KB on GB300), which bounds the lattice long
 // before the tables do: W <= 26 (at L = 1), W = 20 up to L = 8, W = 8 up to
-// L = 80.
+// L = 74.
 #include <mutex>
 
 #include "common.cuh"

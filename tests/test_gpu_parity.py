@@ -290,9 +290,9 @@ def test_mass_wires_into_the_second_fp_unit():
 
 
 def test_mass_wires_resident():
-    """Wires on the largest resident lattice of W = 8 (L = 80), across the
+    """Wires on the largest resident lattice of W = 8 (L = 74), across the
     hexagon and up the fibre, through the resident solver."""
-    _wire_case(8, 80, 16, 47, None, pc.PC_MODE_RESIDENT)
+    _wire_case(8, 74, 16, 47, None, pc.PC_MODE_RESIDENT)
 
 
 # ---------------------------------------------------------------------------
@@ -302,8 +302,8 @@ def test_mass_wires_resident():
 @pytest.mark.parametrize("W,L,p,n", [
     (0, 1, 0.5, 64), (0, 1, 1.0, 4), (0, 5, 0.9, 300), (0, 5, 1.0, 3), (3, 1, 0.2, 200),
     (3, 2, 0.3, 200), (5, 3, 0.0, 50), (5, 3, 1.0, 10), (6, 8, 1.0, 4), (1, 200, 0.9, 100),
-    (8, 80, 0.21, 60),    # largest resident lattice of W = 8
-    (8, 81, 0.21, 60),    # one layer more: streamed
+    (8, 74, 0.21, 60),    # largest resident lattice of W = 8
+    (8, 75, 0.21, 60),    # one layer more: streamed
 ])
 def test_edge_cases(W, L, p, n):
     g = pc.pc_inspect(W, L, p, 21, 0, n)

@@ -77,8 +77,8 @@ def test_static_entry_point_rejects_oversized_requests():
 @pytest.mark.parametrize("W,L,p,n", [
     (26, 1, 0.5, 400),    # the widest lattice the resident solver holds
     (20, 8, 0.3, 300),    # W = 20: its longest resident fibre
-    (12, 40, 0.2, 300),
-    (8, 80, 0.21, 400),   # W = 8: its longest resident fibre
+    (12, 33, 0.2, 300),   # W = 12: its longest resident fibre
+    (8, 74, 0.21, 400),   # W = 8: its longest resident fibre
 ])
 def test_static_entry_point_matches_the_oracle(W, L, p, n):
     """The static tables are built on the device by their own kernel, so they
