@@ -368,8 +368,9 @@ def run_large(args, pc, torch, rank, world, local, dist):
         su_all = int(st_.item())
     value = su_all / t_max
 
-    # end to end through the public call with host outputs (D2H inside)
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    # end to end through the public call with host outputs (D2H inside);
+    # --e2e-steps 0 skips it (profiling runs only)
+    e2e_steps = min(args.steps, args.e2e_steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     su_e2e = 0
@@ -416,7 +417,7 @@ def run_large(args, pc, torch, rank, world, local, dist):
                               "step (every kernel of the solve), peak = measured copy bandwidth "
                               "(MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clk.summary(),
-        "e2e": {"value": su_e2e / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 0,
+        "e2e": {"value": su_e2e / e2e_t if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": len(ps) * (block * (1 + 4 + 4 + 4) + 8)},
         # kernels of each solve: query upload and init, then a sweep and a
         # control kernel per tick
@@ -823,7 +824,8 @@ def main():
     ap.add_argument("--large-configs", type=int, default=64)
     ap.add_argument("--large-block", type=int, default=8,
                     help="configurations per p in one step of the large workload")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2,
+                    help="large workload: steps timed end to end with host outputs (0 = none, profiling only)")
     ap.add_argument("--batch-configs", type=int, default=10_000)
     ap.add_argument("--bits-only", action="store_true",
                     help="verdicts only (PC_BITS_ONLY): the reached-set propagation without the FP32 recursion")

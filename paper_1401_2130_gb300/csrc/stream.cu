@@ -258,33 +258,40 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
 }
 
 
-// Ring state carried across the FP units of one CTA.
+// Ring state carried across the FP units of one CTA.  Planes are copied
+// and consumed strictly in order, round robin over the nring slots, across
+// units too, so the slot of the next plane to consume and the parity of its
+// barrier's phase follow from one cursor; the producer (thread 0) keeps its
+// own slot cursor.  Every plane a unit issues is consumed by the same unit.
 struct Ring {
-  uint32_t ph;    // expected parity of each slot's barrier (identical in all threads)
-  uint32_t pend;  // thread 0: slots with a copy issued and not yet waited for
-  int base;       // slot of the next unit's first plane (identical in all threads)
+  int slot;       // slot of the next plane to consume (identical in all threads)
+  uint32_t par;   // parity of that slot's current phase (flips once per round)
+  int wslot;      // thread 0: slot of the next plane to issue
+  int pending;    // thread 0: planes issued and not yet consumed
   bool dead;      // this thread saw a wait expire: no further waits or copies
 };
+
+__device__ __forceinline__ void ring_next(int& slot, uint32_t& par, int nring) {
+  if (++slot == nring) { slot = 0; par ^= 1u; }
+}
 
 // One FP unit: strips [k0, k0 + kCols) (one per thread) over layers
 // [t0, t1).  Layer t reads planes t+2, t+3 of nu and layer t of the degrees
 // (planes t+1 and older are already in registers).  The segment [lo, hi) of
 // each plane the chunk touches, and the same byte range of the degree layer
 // three planes below it, are copied into the next ring slot by thread 0
-// (cp.async.bulk; an mbarrier per slot counts the bytes).  Planes take ring
-// slots in the order they are copied, continuing across units: plane t0+1 of
-// this unit is in slot rg.base.  After each pair of layers a block barrier
-// frees the slots of the two planes the pair is done with and thread 0
-// refills them nring planes further on, so the copies run at least nring-3
-// layers ahead of their use.  A wait that expires sets
-// error bit 2 and *abort; the thread then skips all further waits and
-// copies, and the kernel drains the copies in flight and returns after the
-// unit.
+// (cp.async.bulk; an mbarrier per slot counts the bytes).  After each pair
+// of layers a block barrier frees the slots of the two planes the pair is
+// done with and thread 0 refills them nring planes further on, so the copies
+// run nring-2 planes ahead of their use.  A wait that expires sets error
+// bit 2 and *abort; the thread then skips all further waits and copies, and
+// the kernel drains the copies in flight and returns after the unit.
 __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat, const SlotView& v, bool odd,
                                                int k0, int t0, int t1, float* ring, uint8_t* dring,
                                                uint64_t* full, Ring& rg, int* abort, const float* inv,
                                                int* s_red) {
   const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap, nring = x.nring;
+  const bool producer_warp = tid < 32;
   // threads past the last strip repeat it: they write the same values to
   // the same addresses, and the layer loop needs no per-thread branch
   const int k = min(k0 + tid, lat.n_strips - 1);
@@ -315,40 +322,43 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   }
   const float* src = odd ? v.nu0 : v.nu1;
   float* dst = odd ? v.nu1 : v.nu0;
+  // thread 0: copy the next plane pl (and the degree layer pl - 3) into its slot
+  int next_pl = t0 + 1;
   const int last = t1 + 2;
-  auto inc = [nring](int s) { return s + 1 == nring ? 0 : s + 1; };
-  // thread 0: copy plane pl (and the degree layer pl - 3) into slot sl
-  auto issue = [&](int pl, int sl) {
-    if (tid != 0 || rg.dead || pl > last) return;
-    rg.pend |= 1u << sl;
-    const int lay = pl - 3;
+  auto issue = [&]() {
+    if (tid != 0 || rg.dead || next_pl > last) return;
+    const int sl = rg.wslot;
+    const int lay = next_pl - 3;
     const bool with_dg = lay >= t0;
     fence_proxy_async_shared();
     mbar_arrive_expect_tx(&full[sl], (unsigned)seg * (with_dg ? 5u : 4u));
-    bulk_g2s(ring + (size_t)sl * cap, src + (size_t)pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
+    bulk_g2s(ring + (size_t)sl * cap, src + (size_t)next_pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
     if (with_dg) bulk_g2s(dring + (size_t)sl * cap, v.dg + (size_t)lay * P + lo_al, (unsigned)seg, &full[sl]);
+    ++next_pl;
+    ++rg.pending;
+    if (++rg.wslot == nring) rg.wslot = 0;
   };
-  auto wait = [&](int sl) {
-    if (rg.dead) return;
-    if (!mbar_wait(&full[sl], (rg.ph >> sl) & 1u)) {
-      rg.dead = true; *abort = 1; atomicOr(x.error, 2);
-      return;
+  // consume the next plane: wait for its slot; returns the slot.  After an
+  // expired wait the cursor stays on that slot, where the drain starts.
+  auto consume = [&]() -> int {
+    const int sl = rg.slot;
+    if (!rg.dead) {
+      if (mbar_wait(&full[sl], rg.par)) {
+        ring_next(rg.slot, rg.par, nring);
+        if (tid == 0) --rg.pending;
+      } else {
+        rg.dead = true; *abort = 1; atomicOr(x.error, 2);
+      }
     }
-    rg.ph ^= 1u << sl;
-    rg.pend &= ~(1u << sl);
+    return sl;
   };
   const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
   const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al, g0 = b - lo_al;
 
-  {
-    int sl = rg.base;
-    for (int i = 1; i <= nring; ++i, sl = inc(sl)) issue(t0 + i, sl);
-  }
-  const int s1 = rg.base;  // plane t0 + 1
-  int s2 = inc(s1);        // plane t + 2
-  int s3 = inc(s2);        // plane t + 3
-  wait(s1);
-  wait(s2);
+  if (producer_warp)
+    for (int i = 0; i < nring; ++i) issue();
+  const int s1 = consume();  // plane t0 + 1
+  int s2 = consume();        // plane t0 + 2
   float up2, dp2, cp[4];
   Runs A, B;
   {
@@ -359,46 +369,47 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     load_runs(A, ring + (size_t)s2 * cap, u0, d0, c0);
   }
   __syncthreads();  // plane t0 + 1's slot is free
-  issue(t0 + 1 + nring, s1);
+  if (producer_warp) issue();
+  // output plane of layer t (global stores, bypassing L1)
+  float* out = dst + (size_t)(t0 + 2) * P + b;
   // layers in pairs: one block barrier frees the two planes the pair is done with
   int t = t0;
   for (;;) {
-    wait(s3);
     {
-      load_runs(B, ring + (size_t)s3 * cap, u0, d0, c0);
+      const int s3 = consume();  // plane t + 3
+      const float* pl3 = ring + (size_t)s3 * cap;
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      strip_emit_deg(A, B, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
-                     dg[0], dg[1], dg[2], inv);
+      load_runs(B, pl3, u0, d0, c0);
+      const float* pl2 = ring + (size_t)s2 * cap;
+      strip_emit_deg_global(A, B, up2, dp2, cp, pl2, e0, f0, out, dg[0], dg[1], dg[2], inv);
       up2 = A.U[2]; dp2 = A.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
+      s2 = s3;
+      out += P;
     }
-    const int fa = s2;  // plane t + 2: done
-    s2 = s3; s3 = inc(s3);
     if (++t >= t1) {
       __syncthreads();
-      issue(t + 1 + nring, fa);
+      if (producer_warp) issue();
       break;
     }
-    wait(s3);
     {
-      load_runs(A, ring + (size_t)s3 * cap, u0, d0, c0);
+      const int s3 = consume();
+      const float* pl3 = ring + (size_t)s3 * cap;
       const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      strip_emit_deg(B, A, up2, dp2, cp, ring + (size_t)s2 * cap, e0, f0, dst + (size_t)(t + 2) * P, b,
-                     dg[0], dg[1], dg[2], inv);
+      load_runs(A, pl3, u0, d0, c0);
+      const float* pl2 = ring + (size_t)s2 * cap;
+      strip_emit_deg_global(B, A, up2, dp2, cp, pl2, e0, f0, out, dg[0], dg[1], dg[2], inv);
       up2 = B.U[2]; dp2 = B.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
+      s2 = s3;
+      out += P;
     }
-    const int fb = s2;  // plane t + 2: done
-    s2 = s3; s3 = inc(s3);
-    __syncthreads();    // planes t + 1 and t + 2 are free
-    issue(t + 1 + nring, fa);
-    issue(t + 2 + nring, fb);
+    __syncthreads();  // planes t + 1 and t + 2 are free
+    if (producer_warp) { issue(); issue(); }
     if (++t >= t1) break;
   }
-  // s2 now holds plane t1 + 2 (the last); the next unit continues after it
-  rg.base = inc(s2);
 }
 
 __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
@@ -418,7 +429,7 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
     mbar_fence_init();
   }
   __syncthreads();
-  Ring rg{0u, 0u, 0, false};
+  Ring rg{0, 0u, 0, 0, false};
   const int total = x.pre[x.K];
   // units are taken from a tick-wide counter (double-buffered broadcast: one
   // block barrier per unit)
@@ -455,8 +466,10 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
       __syncthreads();
       if (s_abort) {  // a wait expired: let the copies in flight land (bounded), then stop
         if (tid == 0)
-          for (int sl = 0; sl < x.nring; ++sl)
-            if ((rg.pend >> sl) & 1u) mbar_wait(&bars[sl], (rg.ph >> sl) & 1u);
+          for (; rg.pending > 0; --rg.pending) {
+            mbar_wait(&bars[rg.slot], rg.par);
+            ring_next(rg.slot, rg.par, x.nring);
+          }
         return;
       }
     } else if (kind == U_BITS) {

@@ -62,6 +62,28 @@ __device__ __forceinline__ void strip_emit_deg(const Runs& c, const Runs& n, flo
   out_pl[b + 2] = inv[g2] * s2;
 }
 
+// As strip_emit_deg, for an output in global memory: out points at the
+// strip's first position; the stores bypass L1 (the next step reads the
+// plane back through a bulk copy).
+__device__ __forceinline__ void strip_emit_deg_global(const Runs& c, const Runs& n, float up2, float dp2,
+                                                      const float (&cp)[4], const float* __restrict__ plc,
+                                                      int e0, int f0, float* __restrict__ out,
+                                                      int g0, int g1, int g2,
+                                                      const float* __restrict__ inv) {
+  const float e_0 = plc[e0], e_1 = plc[e0 + 1], e_2 = plc[e0 + 2];
+  const float f_0 = plc[f0], f_1 = plc[f0 + 1], f_2 = plc[f0 + 2];
+  const float q13 = (c.U[1] + c.U[3]) + (c.D[1] + c.D[3]);
+  const float q24 = (c.U[2] + c.U[4]) + (c.D[2] + c.D[4]);
+  const float s0 = ((q13 + (c.U[0] + up2)) + ((c.D[0] + dp2) + (c.C[2] + cp[0]))) +
+                   ((cp[1] + n.C[1]) + (e_0 + f_0));
+  const float s1 = (q13 + q24) + (((c.C[3] + c.C[1]) + (cp[2] + n.C[2])) + (e_1 + f_1));
+  const float s2 = ((q24 + (c.U[5] + n.U[3])) + ((c.D[5] + n.D[3]) + (n.C[4] + c.C[2]))) +
+                   ((cp[3] + n.C[3]) + (e_2 + f_2));
+  __stcg(out, inv[g0] * s0);
+  __stcg(out + 1, inv[g1] * s1);
+  __stcg(out + 2, inv[g2] * s2);
+}
+
 // As strip_emit_deg, with the degrees read from the layer's degree plane dgl.
 __device__ __forceinline__ void strip_emit(const Runs& c, const Runs& n, float up2, float dp2,
                                            const float (&cp)[4], const float* __restrict__ plc,

@@ -228,7 +228,7 @@ MASS_CASES = [(W, L, p) for W in (16, 32, 64) for L in (1, 4, 8, 16, 24) for p i
 @pytest.mark.parametrize("W,L,p", MASS_CASES)
 def test_mass_relative_both_solvers(W, L, p):
     """Eqs. (3)-(4): the FP32 mass of every configuration within the relative
-    bound of the FP64 oracle.  Lattices of 4 (W = 16) to 18 (W = 64)
+    bound of the FP64 oracle.  Lattices of 2 (W = 16) to 17 (W = 64)
     256-strip FP chunks, every plane cycled through the streamed solver's
     ring; at these lengths every oracle mass is above the floor, so no
     configuration escapes the relative check."""
@@ -274,7 +274,7 @@ def _wire_case(W, L, n, seed, spread, mode):
 
 def test_mass_wires_across_the_wide_lattice():
     """W = 64, L = 60: single induced paths of metallic sites steered through
-    random waypoints anywhere in the hexagon, so they cross many of the 18
+    random waypoints anywhere in the hexagon, so they cross many of the 17
     strip chunks and rows of the streamed solver's FP units.  The masses are
     2^-75 .. 2^-149, far beyond where random configurations keep any FP32
     mass, and both sides must give them exactly."""
