@@ -166,13 +166,13 @@ def cpu_sample(per_p: int, threads: int, cfg0: int = 0, results: list | None = N
     return su, t
 
 
-def sample_parity(pc, refs, per_p: int) -> dict:
+def sample_parity(pc, refs, per_p: int, **kw) -> dict:
     """The CUDA path's outputs on the oracle's sample (configurations
     0..per_p-1 at each p, host outputs, outside every timed region):
     verdicts, first_hit and m_stop must be equal, mass within 1e-5."""
     bad, err, n_gpu, n_ref = 0, 0.0, 0, 0
     for p, r in zip(PS, refs):
-        g = pc.pc_inspect(W, L, p, SEED, 0, per_p)
+        g = pc.pc_inspect(W, L, p, SEED, 0, per_p, **kw)
         same = ((g["verdict"].astype(np.int32) == r["verdict"]) & (g["first_hit"] == r["first_hit"])
                 & (g["m_stop"] == r["m_stop"]))
         bad += int((~same).sum())
@@ -505,8 +505,9 @@ def run_batch(args, pc, torch):
     with Clocks(0) as clk:
         tb = timed(batched, args.steps)
         tp = timed(plain, args.steps)
-    # where the plain time goes: each per-size launch timed alone
-    per_query_ms = {}
+    # where the plain time goes: each per-size launch timed alone, with its
+    # site-update rate and solver
+    per_query_ms, per_query_su_s = {}, {}
     for sp, o in zip(specs, plain_outs):
         W_, L_, p_, seed_, b_, n_ = sp
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -514,7 +515,11 @@ def run_batch(args, pc, torch):
         pc.pc_inspect(W_, L_, p_, seed_, b_, n_, device=True, out=o, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        per_query_ms[f"{W_},{L_}"] = round(e0.elapsed_time(e1), 3)
+        ms = e0.elapsed_time(e1)
+        h = {k: v.cpu().numpy() for k, v in o.items()}
+        su_q = site_updates(3 * W_ * (W_ + 1) + 1, L_, h["verdict"], h["first_hit"], h["m_stop"])
+        per_query_ms[f"{W_},{L_}"] = round(ms, 3)
+        per_query_su_s[f"{W_},{L_}"] = float(f"{su_q / (ms / 1e3):.4g}")
     # a naive GPU path for contrast: one configuration per launch, on a
     # sample of each size's configurations (extrapolated per configuration)
     n_one = 8
@@ -546,7 +551,7 @@ def run_batch(args, pc, torch):
                    "queries": len(specs), "configs_per_query": args.batch_configs,
                    "l2": "no flush (per-launch working sets differ; see plain)"},
         "plain_configs_per_s": n_tot / tp, "batched_over_plain": tp / tb,
-        "plain_ms_per_query": per_query_ms,
+        "plain_ms_per_query": per_query_ms, "plain_site_updates_per_s": per_query_su_s,
         "one_config_per_launch": {"configs_per_s": n_tot / t_one, "batched_over": t_one / tb,
                                   "sample": f"first {n_one} configurations of each size, extrapolated"},
         "site_updates_per_s_batched": su / tb, "results_identical": bool(same),
@@ -687,18 +692,22 @@ def run_psweep(args, pc, torch, rank, world, local, dist):
         for i, p in enumerate(PS):
             if evs is not None:
                 evs[i][0].record(stream)
-            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=True, out=outs[i], stream=stream)
+            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=True, out=outs[i], stream=stream,
+                          verdict_first=args.verdict_first)
             if evs is not None:
                 evs[i][1].record(stream)
 
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
-    # per-configuration work of one step (identical every step: same inputs)
-    su_step = 0
+    # per-configuration work of one step (identical every step: same inputs);
+    # with --verdict-first the FP32 recursion runs on percolating ones only
+    su_step, su_fp = 0, 0
     for i, p in enumerate(PS):
         o = {k: v.cpu().numpy() for k, v in outs[i].items()}
         su_step += site_updates(A_COLS, L, o["verdict"], o["first_hit"], o["m_stop"])
+        pm = o["verdict"] != 0
+        su_fp += site_updates(A_COLS, L, o["verdict"][pm], o["first_hit"][pm], o["m_stop"][pm])
     n_perc = [int(outs[i]["n_percolating"].item()) for i in range(len(PS))]
 
     step_ms, launch_ms = [], []
@@ -739,7 +748,7 @@ def run_psweep(args, pc, torch, rank, world, local, dist):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for p in PS:
-            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=False)
+            pc.pc_inspect(W, L, p, SEED, cfg0, n_cfg, device=False, verdict_first=args.verdict_first)
     e2e_t = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
         tt = torch.tensor([e2e_t], device="cuda")
@@ -787,6 +796,25 @@ def run_psweep(args, pc, torch, rank, world, local, dist):
         "per_p_ms": [float(np.mean(launch_ms[i::len(PS)])) for i in range(len(PS))],
         "wall_s_timed": wall,
     }
+    if args.verdict_first:
+        # the reached set runs over every configuration's causal window, the
+        # FP32 recursion over the percolating ones' only: report configurations
+        # per second, and the site-updates each part performed
+        t_launch = sum(launch_ms) / len(step_ms) / 1e3
+        line["metric"], line["unit"] = "configs/s", "configs/s"
+        line["value"] = n_cfg * len(PS) * world / t_step
+        line["config"]["mode"] = "verdict first (PC_VERDICT_FIRST)"
+        line["site_updates_per_s"] = {"fp32_performed": su_fp / t_launch, "reached_set": su_step / t_launch,
+                                      "single_pass_equivalent": su_step / t_launch}
+        bytes_ = HBM_BYTES_PER_SU * su_fp + BITS_BYTES_PER_SU * su_step
+        line["roofline"]["achieved"] = bytes_ / t_launch / 1e9
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+        line["roofline"]["model"] = (f"{HBM_BYTES_PER_SU} B per FP32 site-update performed + "
+                                     f"{BITS_BYTES_PER_SU} B per reached-set site-update / CUDA-event time; "
+                                     + line["roofline"]["model"].split("; ", 1)[1])
+        line["roofline"].pop("gather_model", None)
+        line["e2e"]["value"] = n_cfg * len(PS) * world / e2e_t
+        line["e2e"]["unit"] = "configs/s"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         refs = []
@@ -794,10 +822,14 @@ def run_psweep(args, pc, torch, rank, world, local, dist):
         line["cpu_baseline"] = {"value": su / t, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{args.cpu_per_p} configurations per p x {len(PS)} p, "
                                           f"Markov mode (FP64 CSR), {t:.1f} s"}
+        if args.verdict_first:
+            line["cpu_baseline"]["value"] = args.cpu_per_p * len(PS) / t
+            line["cpu_baseline"]["unit"] = "configs/s"
         # verdict and Pi parity on the same sample (first configurations of
         # the timed workload)
         try:
-            line["parity"] = sample_parity(pc, refs, args.cpu_per_p)
+            line["parity"] = sample_parity(pc, refs, args.cpu_per_p,
+                                           **({"verdict_first": True} if args.verdict_first else {}))
         except Exception as e:  # reported in the line, never silently dropped
             line["parity"] = {"ok": False, "error": repr(e)}
     return line
@@ -827,6 +859,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2,
                     help="large workload: steps timed end to end with host outputs (0 = none, profiling only)")
     ap.add_argument("--batch-configs", type=int, default=10_000)
+    ap.add_argument("--verdict-first", action="store_true",
+                    help="psweep: PC_VERDICT_FIRST (FP32 recursion on percolating configurations only)")
     ap.add_argument("--bits-only", action="store_true",
                     help="verdicts only (PC_BITS_ONLY): the reached-set propagation without the FP32 recursion")
     ap.add_argument("--large-p", default=None,

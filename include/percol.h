@@ -75,6 +75,17 @@ typedef int32_t pc_status;
                                   reached set decides exactly; verdicts,
                                   first_hit, m_stop and n_percolating equal the
                                   full inspection's, mass is written 0 */
+#define PC_VERDICT_FIRST 0x80  /* the same outputs as the full inspection, to
+                                  the bit, with less work: only configurations
+                                  that percolate have a non-zero mass (the
+                                  detector probability is exactly 0 otherwise,
+                                  Sec. II.B), so the reached set decides every
+                                  configuration first and the FP32 recursion
+                                  then runs, for exactly first_hit - 1 steps,
+                                  on the percolating ones only.  Applies to the
+                                  resident solver; the streamed solver accepts
+                                  the flag and runs its single pass.  Ignored
+                                  with PC_BITS_ONLY */
 
 /*
  * Lattice size (Sec. II.A): n_columns = A = 3W(W+1)+1, n_sites = A*L.
@@ -120,8 +131,8 @@ pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t 
  *               whose reached set did not grow; 0 if no start site is metallic
  * n_percolating (int64) and Pi (= n_percolating / n_configs) are optional.
  * Outputs are host pointers unless flags has PC_OUT_DEVICE.  flags may also
- * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, and PC_BITS_ONLY; any other
- * bit is PC_ERR_ARG.
+ * hold one of PC_MODE_RESIDENT / PC_MODE_STREAM, PC_BITS_ONLY and
+ * PC_VERDICT_FIRST; any other bit is PC_ERR_ARG.
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL, and
  * PC_ERR_TIMEOUT if a bounded device wait of the streamed solver expires
  * (host outputs only: with PC_OUT_DEVICE the call returns before the device
@@ -183,7 +194,8 @@ typedef struct pc_result {
  * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
- * applies to every query of the batch; any other flag bit is PC_ERR_ARG.
+ * and PC_VERDICT_FIRST apply to every query of the batch; any other flag bit
+ * is PC_ERR_ARG.
  * Results equal those of pc_inspect on each query.
  * Threads: calls from several host threads are safe.  A cached batch is
  * reference counted, so evicting it (or pc_shutdown) never frees one that a

@@ -29,6 +29,7 @@ PC_ASYNC = 0x2
 PC_MODE_RESIDENT = 0x10
 PC_MODE_STREAM = 0x20
 PC_BITS_ONLY = 0x40
+PC_VERDICT_FIRST = 0x80
 
 _STATUS = {PC_ERR_ARG: "PC_ERR_ARG", PC_ERR_OOM: "PC_ERR_OOM", PC_ERR_CUDA: "PC_ERR_CUDA",
            PC_ERR_TIMEOUT: "PC_ERR_TIMEOUT", PC_ERR_BUSY: "PC_ERR_BUSY",
@@ -188,11 +189,14 @@ ALL_OUTPUTS = ("first_hit", "mass", "m_stop")
 
 def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs: int, *,
                device: bool = False, want: tuple = ALL_OUTPUTS, mode: int = 0,
-               stream=None, out: dict | None = None, bits_only: bool = False) -> dict:
+               stream=None, out: dict | None = None, bits_only: bool = False,
+               verdict_first: bool = False) -> dict:
     """Inspect configurations config_begin..+n_configs-1 (Sec. II.B, Eqs. (1)-(4)).
 
     bits_only: propagate the exact reached set alone (verdicts, first_hit,
     m_stop; mass is 0).
+    verdict_first: the same outputs, bit for bit, with the FP32 recursion run
+    only on the configurations that percolate (resident solver).
 
     device=False: numpy outputs plus ``n_percolating`` and ``Pi`` (the call
     synchronises).  device=True: torch CUDA tensors written asynchronously on
@@ -200,7 +204,8 @@ def pc_inspect(W: int, L: int, p: float, seed: int, config_begin: int, n_configs
     ``out`` may pass preallocated outputs of the same form.
     """
     o = out if out is not None else _alloc_outputs(n_configs, device, want)
-    flags = mode | (PC_OUT_DEVICE if device else 0) | (PC_BITS_ONLY if bits_only else 0)
+    flags = (mode | (PC_OUT_DEVICE if device else 0) | (PC_BITS_ONLY if bits_only else 0)
+             | (PC_VERDICT_FIRST if verdict_first else 0))
     npc = ctypes.c_int64(0); pi = ctypes.c_double(0.0)
     _check(load().pc_inspect(
         W, L, float(p), int(seed) & (2**64 - 1), config_begin, n_configs,
@@ -308,7 +313,8 @@ def batch_queries(specs, *, device: bool, outs: list | None = None):
 
 
 def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=None,
-                 outs: list | None = None, queries=None, bits_only: bool = False):
+                 outs: list | None = None, queries=None, bits_only: bool = False,
+                 verdict_first: bool = False):
     """Inspect a batch of queries [(W, L, p, seed, config_begin, n_configs)] in
     one submission (one cached CUDA graph).  Returns (outs, results): per-query
     outputs (numpy, or torch CUDA tensors with ``device``) and the host
@@ -316,7 +322,8 @@ def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=No
     ``queries``) again replays the cached graph."""
     if queries is None:
         queries, outs = batch_queries(specs, device=device, outs=outs)
-    flags = (PC_OUT_DEVICE if device else 0) | (PC_ASYNC if async_ else 0) | (PC_BITS_ONLY if bits_only else 0)
+    flags = ((PC_OUT_DEVICE if device else 0) | (PC_ASYNC if async_ else 0) | (PC_BITS_ONLY if bits_only else 0)
+             | (PC_VERDICT_FIRST if verdict_first else 0))
     res = None if async_ else (PcResult * len(specs))()
     _check(load().pc_batch_run(ctypes.addressof(queries), len(specs),
                                None if res is None else ctypes.addressof(res), flags,

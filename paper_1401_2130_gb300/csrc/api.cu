@@ -85,7 +85,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
                        int32_t* first_hit, float* mass, int32_t* m_stop,
                        int64_t* n_percolating, double* Pi, int32_t flags, void* stream) {
   const bool dev_out = (flags & PC_OUT_DEVICE) != 0;
-  if (flags & ~(PC_OUT_DEVICE | PC_MODE_RESIDENT | PC_MODE_STREAM | PC_BITS_ONLY)) {
+  if (flags & ~(PC_OUT_DEVICE | PC_MODE_RESIDENT | PC_MODE_STREAM | PC_BITS_ONLY | PC_VERDICT_FIRST)) {
     set_error("unknown flag bits"); return PC_ERR_ARG;
   }
   if (!verdicts && n > 0) { set_error("verdicts must not be NULL"); return PC_ERR_ARG; }
@@ -151,6 +151,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       a.verdict = s.verdict; a.first_hit = s.first_hit; a.mass = s.mass; a.m_stop = s.m_stop;
       a.n_perc = s.n_perc; a.work = s.work; a.prep_chunk = 8;
       a.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
+      a.verdict_first = (flags & PC_VERDICT_FIRST) ? 1 : 0;
       rc = launch_resident(a, tuned_threads(lat, occ_bits ? 0.2 : p, seed, st), st);
     } else {
       StreamJob j;

@@ -233,6 +233,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         a.verdict = P.v; a.first_hit = P.fh; a.mass = P.mass; a.m_stop = P.ms;
         a.n_perc = P.n_perc; a.work = ctr + 2 * i + 1; a.prep_chunk = 8;
         a.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
+        a.verdict_first = (flags & PC_VERDICT_FIRST) ? 1 : 0;
         if (!a.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
         cudaGraphNode_t node;
         rc = resident_add_node(a, P.threads, b->graph, &n_zero, 1, &node);
@@ -287,7 +288,7 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
                                   void* cuda_stream) {
   NvtxRange nvtx_("pc_batch_run");
   if (nq < 0 || (nq > 0 && !q)) { set_error("pc_batch_run: bad query array"); return PC_ERR_ARG; }
-  if (flags & ~(PC_OUT_DEVICE | PC_ASYNC | PC_BITS_ONLY)) { set_error("pc_batch_run: unknown flag bits"); return PC_ERR_ARG; }
+  if (flags & ~(PC_OUT_DEVICE | PC_ASYNC | PC_BITS_ONLY | PC_VERDICT_FIRST)) { set_error("pc_batch_run: unknown flag bits"); return PC_ERR_ARG; }
   const bool dev_out = (flags & PC_OUT_DEVICE) != 0, async = (flags & PC_ASYNC) != 0;
   if (async && (!dev_out || out)) { set_error("PC_ASYNC needs PC_OUT_DEVICE and out == NULL"); return PC_ERR_ARG; }
   for (int64_t i = 0; i < nq; ++i) {

@@ -30,6 +30,7 @@ struct ResidentArgs {
   unsigned long long* work;  // zeroed work counter
   int prep_chunk;            // layers prepared per lazy chunk (>= 3)
   int bits_only = 0;         // reached set only: no FP32 sweep, mass written 0
+  int verdict_first = 0;     // reached set first, FP32 recursion only where it percolates
 };
 constexpr int kResidentMaxThreads = 640;  // resident CTA size limit: 20 warps at <= 96 registers
 size_t resident_smem(const Lattice& lat);

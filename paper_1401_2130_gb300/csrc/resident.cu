@@ -141,19 +141,38 @@ __device__ inline long long block_sum_i(long long v, long long* red) {
   return s;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
 // bit of a word array [tw + 1][S]: column col, tube tt (tt = -1 and tt >= L
 // land in zero padding)
 __device__ inline uint32_t bit_at(const uint32_t* w, int S, int col, int tt) {
   return (w[((tt >> 5) + 1) * S + col] >> (tt & 31)) & 1u;
 }
 
-// Word of R at tube offset dt, aligned to the word tw of the caller:
-// bit b of the result = R(col, 32*tw + b + dt).
-__device__ inline uint32_t shifted_word(const uint32_t* R, int S, int col, int tw, int dt) {
-  const uint32_t w = R[(tw + 1) * S + col];
-  if (dt == 0) return w;
-  if (dt > 0) return (w >> 1) | (R[(tw + 2) * S + col] << 31);
-  return (w << 1) | (R[tw * S + col] >> 31);
+// Contacts of word tw of column col in the reached set R (words [tw + 1][S]):
+// bit b of the result is set when some contact of the site at tube
+// 32*tw + b is in R.  The end contacts are the own column at tubes t-1 and
+// t+1; the 6 same-layer contacts share the tube index; the 3 up contacts
+// are at tube t+1 when sigma = 2, the 3 down contacts at t-1 when
+// sigma = 0.  Each group of three is ORed first and shifted once by a
+// funnel shift selected by sigma, so no lane branches on its sublattice.
+__device__ __forceinline__ uint32_t contact_word(const uint32_t* R, int S, int col, int tw,
+                                                 const int (&nb)[kLateral], uint32_t sh_up,
+                                                 uint32_t sh_dn) {
+  const uint32_t* r0 = R + tw * S;  // word tw - 1
+  const uint32_t* r1 = r0 + S;      // word tw
+  const uint32_t* r2 = r1 + S;      // word tw + 1
+  const uint32_t own = r1[col];
+  uint32_t acc = ((own << 1) | (r0[col] >> 31)) | ((own >> 1) | (r2[col] << 31));
+#pragma unroll
+  for (int d = 0; d < 6; ++d) acc |= r1[nb[d]];
+  const uint32_t up = r1[nb[6]] | r1[nb[7]] | r1[nb[8]];
+  const uint32_t up_hi = r2[nb[6]] | r2[nb[7]] | r2[nb[8]];
+  const uint32_t dn = r1[nb[9]] | r1[nb[10]] | r1[nb[11]];
+  const uint32_t dn_lo = r0[nb[9]] | r0[nb[10]] | r0[nb[11]];
+  return acc | __funnelshift_r(up, up_hi, sh_up) | __funnelshift_l(dn_lo, dn, sh_dn);
 }
 
 // Lazy preparation of layers [F, Fnew): occupancy drawn up to layer Fnew (for
@@ -245,6 +264,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
 
   const int CH = Pa.prep_chunk;
   const bool bits_only = Pa.bits_only != 0;
+  // verdict first: the reached set alone decides every configuration, and
+  // the FP32 recursion runs afterwards, for exactly first_hit - 1 steps,
+  // only on the configurations that percolate (the others' mass is 0)
+  const bool vfirst = Pa.verdict_first != 0 && !bits_only && L > 1;
+  const bool no_fp = bits_only || vfirst;  // no FP32 sweep in the first pass
   const int n_words_col = S * TWP;
   // when the CTA has a thread per column, that thread owns the column's
   // reached-set words and keeps its neighbour table (packed int16 pairs)
@@ -276,7 +300,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
     os.cfg = cfg;
     const uint32_t* cbits = Pa.occ_bits ? Pa.occ_bits + (size_t)rel * Pa.words_per_cfg : nullptr;
 
-    prepare_layers(sm, lat, os, cbits, G, F, min(max(CH, 3), L), bits_only);
+    prepare_layers(sm, lat, os, cbits, G, F, min(max(CH, 3), L), no_fp);
+
+    // FP32 sweep of step m over the causal window: (strip, layer chunk)
+    // items; K chunks per strip so that every thread gets at most one item
+    // when the window allows.  The strip index is padded to a multiple of 32
+    // per chunk (lanes past NS idle): a warp then never holds strips of two
+    // chunks, whose planes lie whole planes apart and would share banks.
+    auto fp_sweep = [&](int m, const float* src, float* dst) {
+      const int nl = min(m, L - 1) + 1;
+      const int NSp = (NS + 31) & ~31;
+      const int K = T / NSp > 1 ? T / NSp : 1;
+      int CL = (nl + K - 1) / K;
+      CL = CL < 2 ? 2 : CL;
+      const int nch = (nl + CL - 1) / CL;
+      const uint32_t src_s = smem_addr(src), dg_s = smem_addr(sm.dg), inv_s = smem_addr(sm.inv);
+      for (int it = tid; it < NSp * nch; it += T) {
+        const int c = it / NSp, k = it - c * NSp;
+        if (k >= NS) continue;
+        const int t0 = c * CL, t1 = min(t0 + CL, nl);
+        const int* ro = sm.roff + 4 * sm.srow[k];
+        strip_sweep_s(src_s, dst, dg_s, inv_s, P, 3 * (SB + k), ro[0], ro[1], ro[2], ro[3], t0, t1);
+      }
+    };
 
     // ---- m = 0: start distribution on the metallic sites of t = 0 ----
     long long my_n0 = 0;
@@ -290,11 +336,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
     float mass = 0.f;
     if (n0 > 0) {
       const float inv_n0 = __frcp_rn((float)n0);
-      for (int a = bits_only ? A : tid; a < A; a += T) {
-        const int pos = __ldg(lat.ppos + a);
-        sm.nu[0][2 * P + pos] = (sm.occw[S + a] & 1u) ? sm.inv[sm.dg[pos]] * inv_n0 : 0.f;
-      }
-      __syncthreads();
+      auto start_nu = [&]() {
+        for (int a = tid; a < A; a += T) {
+          const int pos = __ldg(lat.ppos + a);
+          sm.nu[0][2 * P + pos] = (sm.occw[S + a] & 1u) ? sm.inv[sm.dg[pos]] * inv_n0 : 0.f;
+        }
+        __syncthreads();
+      };
+      if (!no_fp) start_nu();
+      else __syncthreads();
       if (L == 1) {
         float part = 0.f;
         for (int k = tid; k < P; k += T) part += sm.nu[0][2 * P + k];
@@ -303,35 +353,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
       } else {
         for (int m = 1;; ++m) {
           const int tmax = min(m, L - 1);
-          if (F < min(m + 3, L)) prepare_layers(sm, lat, os, cbits, G, F, min(max(F + CH, m + 3), L), bits_only);
+          if (F < min(m + 3, L)) prepare_layers(sm, lat, os, cbits, G, F, min(max(F + CH, m + 3), L), no_fp);
           const bool odd = (m & 1) != 0;  // step m reads buffer (m-1)&1, writes m&1
           const float* __restrict__ src = odd ? sm.nu[0] : sm.nu[1];
           float* __restrict__ dst = odd ? sm.nu[1] : sm.nu[0];
           const uint32_t* Rs = odd ? sm.R[0] : sm.R[1];
           uint32_t* Rd = odd ? sm.R[1] : sm.R[0];
-          // FP32 sweep: (strip, layer chunk) items; K chunks per strip so
-          // that every thread gets at most one item when the window allows
-          const int nl = tmax + 1;
-          const int K = T / NS > 1 ? T / NS : 1;
-          int CL = (nl + K - 1) / K;
-          CL = CL < 2 ? 2 : CL;
-          const int nch = (nl + CL - 1) / CL;
-          for (int it = bits_only ? NS * nch : tid; it < NS * nch; it += T) {
-            const int c = it / NS, k = it - c * NS;
-            const int t0 = c * CL, t1 = min(t0 + CL, nl);
-            const int* ro = sm.roff + 4 * sm.srow[k];
-            strip_sweep(src, dst, sm.dg, sm.inv, P, 3 * (SB + k), ro[0], ro[1], ro[2], ro[3], t0, t1);
-          }
+          if (!no_fp) fp_sweep(m, src, dst);
           // exact reached-set step, 32 tubes per word
           const int nwin = (tmax >> 5) + 1;
           const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
           uint32_t fl = 0;
           if (own_col) {  // this thread's column, neighbour table in registers
-            for (int tw = 0; tw < nwin; ++tw) {
-              uint32_t acc = shifted_word(Rs, S, tid, tw, -1) | shifted_word(Rs, S, tid, tw, 1);
+            int nb[kLateral];
 #pragma unroll
-              for (int d = 0; d < kLateral; ++d)
-                acc |= shifted_word(Rs, S, (my_nb[d >> 1] >> ((d & 1) * 16)) & 0xffff, tw, dir_dt(d, my_sg));
+            for (int d = 0; d < kLateral; ++d) nb[d] = (my_nb[d >> 1] >> ((d & 1) * 16)) & 0xffff;
+            const uint32_t sh_up = my_sg == 2 ? 1u : 0u, sh_dn = my_sg == 0 ? 1u : 0u;
+            for (int tw = 0; tw < nwin; ++tw) {
+              const uint32_t acc = contact_word(Rs, S, tid, tw, nb, sh_up, sh_dn);
               const int wi = (tw + 1) * S + tid;
               const uint32_t old = Rs[wi];
               const uint32_t nw = old | (acc & sm.occw[wi]);
@@ -342,10 +381,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
           } else if (T < A) {
             for (int u = tid; u < A * nwin; u += T) {
               const int tw = u / A, a = u - tw * A, sg = sm.sig[a];
-              uint32_t acc = shifted_word(Rs, S, a, tw, -1) | shifted_word(Rs, S, a, tw, 1);
+              int nb[kLateral];
 #pragma unroll
-              for (int d = 0; d < kLateral; ++d)
-                acc |= shifted_word(Rs, S, sm.nbr[a * kLateral + d], tw, dir_dt(d, sg));
+              for (int d = 0; d < kLateral; ++d) nb[d] = sm.nbr[a * kLateral + d];
+              const uint32_t acc = contact_word(Rs, S, a, tw, nb, sg == 2 ? 1u : 0u, sg == 0 ? 1u : 0u);
               const int wi = (tw + 1) * S + a;
               const uint32_t old = Rs[wi];
               const uint32_t nw = old | (acc & sm.occw[wi]);
@@ -361,12 +400,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
           if (tid == 0) sm.flags[(m + 2) % 3] = 0u;
           if (f & kEnd) {
             float part = 0.f;
-            for (int k = bits_only ? P : tid; k < P; k += T) part += dst[(size_t)(L + 1) * P + k];
-            mass = bits_only ? 0.f : block_sum_f(part, sm.redf);
+            for (int k = no_fp ? P : tid; k < P; k += T) part += dst[(size_t)(L + 1) * P + k];
+            mass = no_fp ? 0.f : block_sum_f(part, sm.redf);
             verdict = 1; fh = m + 1; mstop = m + 1;
             break;
           }
           if (!(f & kGrow)) { mstop = m; break; }
+        }
+        if (vfirst && verdict) {
+          // second pass, FP32 only: degrees from layer 0 (the occupancy is
+          // already drawn), nu_0, then steps 1 .. first_hit - 1 exactly as
+          // the single pass runs them, so the mass is the same to the bit
+          F = 0;
+          prepare_layers(sm, lat, os, cbits, G, F, min(max(CH, 3), L), false);
+          start_nu();
+          for (int m = 1; m < fh; ++m) {
+            if (F < min(m + 3, L)) prepare_layers(sm, lat, os, cbits, G, F, min(max(F + CH, m + 3), L), false);
+            const bool odd = (m & 1) != 0;
+            fp_sweep(m, odd ? sm.nu[0] : sm.nu[1], odd ? sm.nu[1] : sm.nu[0]);
+            __syncthreads();
+          }
+          const float* last = ((fh - 1) & 1) ? sm.nu[1] : sm.nu[0];
+          float part = 0.f;
+          for (int k = tid; k < P; k += T) part += last[(size_t)(L + 1) * P + k];
+          mass = block_sum_f(part, sm.redf);
         }
       }
     }

@@ -261,15 +261,20 @@ __global__ void __launch_bounds__(1024) stream_init_kernel(Ctx x) {
 // Ring state carried across the FP units of one CTA.  Planes are copied
 // and consumed strictly in order, round robin over the nring slots, across
 // units too, so the slot of the next plane to consume and the parity of its
-// barrier's phase follow from one cursor; the producer (thread 0) keeps its
-// own slot cursor.  Every plane a unit issues is consumed by the same unit.
+// barrier's phase follow from one cursor, and the slot of the next plane to
+// copy from another.  Every thread keeps both (they are identical in all
+// threads); the copies are issued by lane 0 of the warps in turn.  Every
+// plane a unit issues is consumed by the same unit.
 struct Ring {
-  int slot;       // slot of the next plane to consume (identical in all threads)
+  int slot;       // slot of the next plane to consume
   uint32_t par;   // parity of that slot's current phase (flips once per round)
-  int wslot;      // thread 0: slot of the next plane to issue
-  int pending;    // thread 0: planes issued and not yet consumed
+  int wslot;      // slot of the next plane to copy
+  int pending;    // planes copied and not yet consumed
+  int turn;       // warp that issues the next copy
   bool dead;      // this thread saw a wait expire: no further waits or copies
 };
+
+constexpr int kWarps = kCols / 32;
 
 __device__ __forceinline__ void ring_next(int& slot, uint32_t& par, int nring) {
   if (++slot == nring) { slot = 0; par ^= 1u; }
@@ -279,11 +284,13 @@ __device__ __forceinline__ void ring_next(int& slot, uint32_t& par, int nring) {
 // [t0, t1).  Layer t reads planes t+2, t+3 of nu and layer t of the degrees
 // (planes t+1 and older are already in registers).  The segment [lo, hi) of
 // each plane the chunk touches, and the same byte range of the degree layer
-// three planes below it, are copied into the next ring slot by thread 0
-// (cp.async.bulk; an mbarrier per slot counts the bytes).  After each pair
-// of layers a block barrier frees the slots of the two planes the pair is
-// done with and thread 0 refills them nring planes further on, so the copies
-// run nring-2 planes ahead of their use.  A wait that expires sets error
+// three planes below it, are copied into the next ring slot (cp.async.bulk;
+// an mbarrier per slot counts the bytes).  After each pair of layers a block
+// barrier frees the slots of the two planes the pair is done with, and they
+// are refilled nring planes further on, so the copies run nring-2 planes
+// ahead of their use.  The copies go to the warps in turn: a warp that
+// issues one starts the next pair a few instructions late, and the pair's
+// barrier waits for it, so no warp should carry them all.  A wait that expires sets error
 // bit 2 and *abort; the thread then skips all further waits and copies, and
 // the kernel drains the copies in flight and returns after the unit.
 __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat, const SlotView& v, bool odd,
@@ -291,7 +298,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
                                                uint64_t* full, Ring& rg, int* abort, const float* inv,
                                                int* s_red) {
   const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap, nring = x.nring;
-  const bool producer_warp = tid < 32;
+  const int warp = tid >> 5;
   // threads past the last strip repeat it: they write the same values to
   // the same addresses, and the layer loop needs no per-thread branch
   const int k = min(k0 + tid, lat.n_strips - 1);
@@ -322,21 +329,25 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   }
   const float* src = odd ? v.nu0 : v.nu1;
   float* dst = odd ? v.nu1 : v.nu0;
-  // thread 0: copy the next plane pl (and the degree layer pl - 3) into its slot
+  // copy the next plane (and the degree layer three below it) into its
+  // slot: lane 0 of warp rg.turn issues, every thread advances the cursor
   int next_pl = t0 + 1;
   const int last = t1 + 2;
   auto issue = [&]() {
-    if (tid != 0 || rg.dead || next_pl > last) return;
-    const int sl = rg.wslot;
-    const int lay = next_pl - 3;
-    const bool with_dg = lay >= t0;
-    fence_proxy_async_shared();
-    mbar_arrive_expect_tx(&full[sl], (unsigned)seg * (with_dg ? 5u : 4u));
-    bulk_g2s(ring + (size_t)sl * cap, src + (size_t)next_pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
-    if (with_dg) bulk_g2s(dring + (size_t)sl * cap, v.dg + (size_t)lay * P + lo_al, (unsigned)seg, &full[sl]);
+    if (next_pl > last) return;
+    if (warp == rg.turn && (tid & 31) == 0 && !rg.dead) {
+      const int sl = rg.wslot;
+      const int lay = next_pl - 3;
+      const bool with_dg = lay >= t0;
+      fence_proxy_async_shared();
+      mbar_arrive_expect_tx(&full[sl], (unsigned)seg * (with_dg ? 5u : 4u));
+      bulk_g2s(ring + (size_t)sl * cap, src + (size_t)next_pl * P + lo_al, (unsigned)seg * 4u, &full[sl]);
+      if (with_dg) bulk_g2s(dring + (size_t)sl * cap, v.dg + (size_t)lay * P + lo_al, (unsigned)seg, &full[sl]);
+    }
     ++next_pl;
     ++rg.pending;
     if (++rg.wslot == nring) rg.wslot = 0;
+    if (++rg.turn == kWarps) rg.turn = 0;
   };
   // consume the next plane: wait for its slot; returns the slot.  After an
   // expired wait the cursor stays on that slot, where the drain starts.
@@ -345,7 +356,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     if (!rg.dead) {
       if (mbar_wait(&full[sl], rg.par)) {
         ring_next(rg.slot, rg.par, nring);
-        if (tid == 0) --rg.pending;
+        --rg.pending;
       } else {
         rg.dead = true; *abort = 1; atomicOr(x.error, 2);
       }
@@ -354,60 +365,65 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   };
   const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
   const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al, g0 = b - lo_al;
+  // shared addresses (bytes): slot s of the FP32 ring at ring_s + s * cap4,
+  // of the degree ring at dring_s + s * cap
+  const uint32_t ring_s = smem_u32(ring), dring_s = smem_u32(dring), inv_s = smem_u32(inv);
+  const uint32_t cap4 = 4u * (uint32_t)cap;
 
-  if (producer_warp)
-    for (int i = 0; i < nring; ++i) issue();
+  for (int i = 0; i < nring; ++i) issue();
   const int s1 = consume();  // plane t0 + 1
-  int s2 = consume();        // plane t0 + 2
+  const int s2 = consume();  // plane t0 + 2
   float up2, dp2, cp[4];
   Runs A, B;
   {
-    const float* pl = ring + (size_t)s1 * cap;
-    up2 = pl[u0 + 2]; dp2 = pl[d0 + 2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) cp[i] = pl[c0 + i];
-    load_runs(A, ring + (size_t)s2 * cap, u0, d0, c0);
+    const uint32_t p1 = ring_s + (uint32_t)s1 * cap4;
+    up2 = lds_f<8>(p1 + 4u * (uint32_t)u0); dp2 = lds_f<8>(p1 + 4u * (uint32_t)d0);
+    const uint32_t c1 = p1 + 4u * (uint32_t)c0;
+    cp[0] = lds_f<0>(c1); cp[1] = lds_f<4>(c1); cp[2] = lds_f<8>(c1); cp[3] = lds_f<12>(c1);
+    const uint32_t q2 = ring_s + (uint32_t)s2 * cap4;
+    load_runs_s(A, q2 + 4u * (uint32_t)u0, q2 + 4u * (uint32_t)d0, q2 + 4u * (uint32_t)c0);
   }
   __syncthreads();  // plane t0 + 1's slot is free
-  if (producer_warp) issue();
+  issue();
   // output plane of layer t (global stores, bypassing L1)
   float* out = dst + (size_t)(t0 + 2) * P + b;
   // layers in pairs: one block barrier frees the two planes the pair is done with
   int t = t0;
+  // shared byte address of the slot of plane t + 2
+  uint32_t p2 = ring_s + (uint32_t)s2 * cap4;
   for (;;) {
     {
       const int s3 = consume();  // plane t + 3
-      const float* pl3 = ring + (size_t)s3 * cap;
-      const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      load_runs(B, pl3, u0, d0, c0);
-      const float* pl2 = ring + (size_t)s2 * cap;
-      strip_emit_deg_global(A, B, up2, dp2, cp, pl2, e0, f0, out, dg[0], dg[1], dg[2], inv);
+      const uint32_t p3 = ring_s + (uint32_t)s3 * cap4;
+      load_runs_s(B, p3 + 4u * (uint32_t)u0, p3 + 4u * (uint32_t)d0, p3 + 4u * (uint32_t)c0);
+      strip_emit_s(A, B, up2, dp2, cp, p2 + 4u * (uint32_t)e0, p2 + 4u * (uint32_t)f0,
+                   dring_s + (uint32_t)s3 * (uint32_t)cap + (uint32_t)g0, inv_s, out);
       up2 = A.U[2]; dp2 = A.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
-      s2 = s3;
+      p2 = p3;
       out += P;
     }
     if (++t >= t1) {
       __syncthreads();
-      if (producer_warp) issue();
+      issue();
       break;
     }
     {
       const int s3 = consume();
-      const float* pl3 = ring + (size_t)s3 * cap;
-      const uint8_t* dg = dring + (size_t)s3 * cap + g0;
-      load_runs(A, pl3, u0, d0, c0);
-      const float* pl2 = ring + (size_t)s2 * cap;
-      strip_emit_deg_global(B, A, up2, dp2, cp, pl2, e0, f0, out, dg[0], dg[1], dg[2], inv);
+      const uint32_t p3 = ring_s + (uint32_t)s3 * cap4;
+      load_runs_s(A, p3 + 4u * (uint32_t)u0, p3 + 4u * (uint32_t)d0, p3 + 4u * (uint32_t)c0);
+      strip_emit_s(B, A, up2, dp2, cp, p2 + 4u * (uint32_t)e0, p2 + 4u * (uint32_t)f0,
+                   dring_s + (uint32_t)s3 * (uint32_t)cap + (uint32_t)g0, inv_s, out);
       up2 = B.U[2]; dp2 = B.D[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
-      s2 = s3;
+      p2 = p3;
       out += P;
     }
     __syncthreads();  // planes t + 1 and t + 2 are free
-    if (producer_warp) { issue(); issue(); }
+    issue();
+    issue();
     if (++t >= t1) break;
   }
 }
@@ -429,7 +445,7 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
     mbar_fence_init();
   }
   __syncthreads();
-  Ring rg{0, 0u, 0, 0, false};
+  Ring rg{0, 0u, 0, 0, 0, false};
   const int total = x.pre[x.K];
   // units are taken from a tick-wide counter (double-buffered broadcast: one
   // block barrier per unit)
@@ -488,6 +504,9 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
 #pragma unroll
         for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
         const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
+        // the up contacts reach tube t+1 from sigma = 2, the down contacts
+        // tube t-1 from sigma = 0: one funnel shift of their ORed words
+        const uint32_t sh_up = sg == 2 ? 1u : 0u, sh_dn = sg == 0 ? 1u : 0u;
 #pragma unroll 2
         for (int tw = w0; tw < w1; ++tw) {
           const uint32_t* r0 = Rs + (size_t)tw * S;  // word tw - 1
@@ -496,14 +515,15 @@ __global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
           const uint32_t old = __ldg(r1 + a);
           // end contacts: tubes t-1 and t+1 of the own column
           uint32_t acc = ((old << 1) | (__ldg(r0 + a) >> 31)) | ((old >> 1) | (__ldg(r2 + a) << 31));
+          // same-layer contacts (d = 0..5): same tube index
 #pragma unroll
-          for (int d = 0; d < kLateral; ++d) {
-            const int dt = dir_dt(d, sg);
-            uint32_t w = __ldg(r1 + nb[d]);
-            if (dt > 0) w = (w >> 1) | (__ldg(r2 + nb[d]) << 31);
-            else if (dt < 0) w = (w << 1) | (__ldg(r0 + nb[d]) >> 31);
-            acc |= w;
-          }
+          for (int d = 0; d < 6; ++d) acc |= __ldg(r1 + nb[d]);
+          const uint32_t up = __ldg(r1 + nb[6]) | __ldg(r1 + nb[7]) | __ldg(r1 + nb[8]);
+          const uint32_t up_hi = __ldg(r2 + nb[6]) | __ldg(r2 + nb[7]) | __ldg(r2 + nb[8]);
+          const uint32_t dn = __ldg(r1 + nb[9]) | __ldg(r1 + nb[10]) | __ldg(r1 + nb[11]);
+          const uint32_t dn_lo = __ldg(r0 + nb[9]) | __ldg(r0 + nb[10]) | __ldg(r0 + nb[11]);
+          // bit b of the result = contact at tube 32 tw + b (+1 for up, -1 for down)
+          acc |= __funnelshift_r(up, up_hi, sh_up) | __funnelshift_l(dn_lo, dn, sh_dn);
           const int wi = (tw + 1) * S + a;
           const uint32_t nw = old | (acc & __ldg(occw + wi));
           Rd[wi] = nw;

@@ -85,7 +85,7 @@ def test_inspect_argument_errors_without_gpu(lib):
     assert lib.pc_inspect(4, 16, 0.2, 1, 0, 4, ctypes.addressof(v), None, None, None, None,
                           ctypes.addressof(pi), pc.PC_OUT_DEVICE, None) == pc.PC_ERR_ARG
     # both solvers forced, and flag bits the call does not define
-    for flags in (pc.PC_MODE_RESIDENT | pc.PC_MODE_STREAM, pc.PC_ASYNC, 0x4, 0x80, 1 << 30):
+    for flags in (pc.PC_MODE_RESIDENT | pc.PC_MODE_STREAM, pc.PC_ASYNC, 0x4, 0x100, 1 << 30):
         assert lib.pc_inspect(4, 16, 0.2, 1, 0, 4, ctypes.addressof(v), None, None, None, None,
                               None, flags, None) == pc.PC_ERR_ARG, flags
         assert lib.pc_inspect_occupancy(4, 16, ctypes.addressof(v), 4, ctypes.addressof(v), None,
