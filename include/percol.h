@@ -328,6 +328,17 @@ pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_
                             int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol);
 
 /*
+ * The paired plane layout of the streamed solver (diagnostics and tests;
+ * host only), with the outputs of pc_lattice_layout.  In addition to that
+ * layout's properties, every row offset is even, so a strip pair (plane
+ * positions 6h .. 6h+5) reads its runs with aligned 64-bit loads, and no
+ * strip pair holds columns of two rows; the zero zones before and after the
+ * rows are W + 20 entries long.  Errors: PC_ERR_ARG.
+ */
+pc_status pc_stream_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
+                           int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol);
+
+/*
  * The lazy walk of the self-loop remark in Sec. II.B: at every step the
  * electron stays on its site with probability hold, otherwise it moves as
  * Eq. (2) says (the chain hold * I + (1 - hold) * P).  Percolation, first_hit

@@ -53,6 +53,7 @@ SIGNATURES = {
     "pc_server_get_stats": [_vp, _vp],
     "pc_server_destroy": [_vp],
     "pc_lattice_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pc_stream_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pc_lazy_mass": [_vp, _vp, _i64, _dbl, _vp, _i32, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
@@ -131,6 +132,20 @@ def pc_lattice_layout(W: int) -> dict:
     sr = np.zeros(ns.value, np.int16); ro = np.zeros((2 * W + 1, 4), np.int32)
     pp = np.zeros(A, np.int32); pcl = np.zeros(P.value, np.int32)
     _check(lib.pc_lattice_layout(W, None, None, None, _ptr(sr), _ptr(ro), _ptr(pp), _ptr(pcl)))
+    return {"P": P.value, "s_begin": sb.value, "n_strips": ns.value, "strip_row": sr,
+            "row_off": ro, "ppos": pp, "pcol": pcl}
+
+
+def pc_stream_layout(W: int) -> dict:
+    """Paired plane layout of radius W used by the streamed solver (see percol.h)."""
+    lib = load()
+    P, sb, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.pc_stream_layout(W, ctypes.addressof(P), ctypes.addressof(sb), ctypes.addressof(ns),
+                                None, None, None, None))
+    A = 3 * W * (W + 1) + 1
+    sr = np.zeros(ns.value, np.int16); ro = np.zeros((2 * W + 1, 4), np.int32)
+    pp = np.zeros(A, np.int32); pcl = np.zeros(P.value, np.int32)
+    _check(lib.pc_stream_layout(W, None, None, None, _ptr(sr), _ptr(ro), _ptr(pp), _ptr(pcl)))
     return {"P": P.value, "s_begin": sb.value, "n_strips": ns.value, "strip_row": sr,
             "row_off": ro, "ppos": pp, "pcol": pcl}
 

@@ -100,7 +100,22 @@ struct Lattice {
   const int32_t* row_off;    // [2W+1][4] offsets to rows r-2, r-1, r+1, r+2
   const int32_t* ppos;       // [A] plane position of each column
   const int32_t* pcol;       // [P] column at each plane position, -1 for zeros
+  // the paired layout of the streamed solver (same fields; see lattice.cu)
+  int P2, s_begin2, n_strips2;
+  const int16_t* strip_row2;
+  const int32_t* row_off2;
+  const int32_t* ppos2;
+  const int32_t* pcol2;
 };
+
+// The lattice as the streamed solver sees it: its paired plane layout in
+// place of the compact one.
+inline Lattice stream_view(const Lattice& l) {
+  Lattice v = l;
+  v.P = l.P2; v.s_begin = l.s_begin2; v.n_strips = l.n_strips2;
+  v.strip_row = l.strip_row2; v.row_off = l.row_off2; v.ppos = l.ppos2; v.pcol = l.pcol2;
+  return v;
+}
 
 // Host-side padded-row layout of one W (lattice.cu).
 struct PlaneLayout {
@@ -108,8 +123,10 @@ struct PlaneLayout {
   std::vector<int16_t> strip_row;
   std::vector<int32_t> row_off, ppos, pcol;
 };
-PlaneLayout make_layout(int W);
-int max_segment(int W, int chunk);
+PlaneLayout make_layout(int W, bool paired = false);
+// largest bulk-copy segment (entries, a multiple of 16) that a chunk of
+// `pairs` strip pairs reads in one plane of the paired layout
+int max_pair_segment(int W, int pairs);
 
 // Plane positions [lo, hi) read by the strip at position b whose row has the
 // offsets ro[0..3] (rows r-2, r-1, r+1, r+2): the runs of tiling.cuh.
@@ -123,7 +140,20 @@ __host__ __device__ inline void strip_span(int b, const int32_t* ro, int* lo, in
   *lo = l; *hi = h;
 }
 void layout_fill(int W, int* P, int* s_begin, int* n_strips, int16_t* strip_row, int32_t* row_off,
-                 int32_t* ppos, int32_t* pcol);
+                 int32_t* ppos, int32_t* pcol, bool paired = false);
+
+// Plane positions [lo, hi) read by the strip pair at plane position b (= 6h,
+// paired layout) whose row has the offsets ro[0..3] (rows r-2, r-1, r+1,
+// r+2), with the 64-bit loads of the streamed sweep.
+__host__ __device__ inline void pair_span(int b, const int32_t* ro, int* lo, int* hi) {
+  const int fl = b + ro[0], dl = b - 2 + ro[1], ul = b - 2 + ro[2], el = b - 2 + ro[3], cl = b - 2;
+  int l = cl, h = cl + 10;
+  l = l < fl ? l : fl; h = h > fl + 8 ? h : fl + 8;
+  l = l < dl ? l : dl; h = h > dl + 10 ? h : dl + 10;
+  l = l < ul ? l : ul; h = h > ul + 10 ? h : ul + 10;
+  l = l < el ? l : el; h = h > el + 8 ? h : el + 8;
+  *lo = l; *hi = h;
+}
 
 // NVTX range over a host call (profilers group the call's launches under it)
 struct NvtxRange {

@@ -18,42 +18,56 @@ namespace pc {
 
 int64_t n_columns(int W) { return 3ll * W * (W + 1) + 1; }
 
-// Padded-row plane layout of one tube layer (the FP arrays nu and deg).
-// A zero zone of W + 8 entries opens the plane and stands for the rows -W-2,
-// -W-1 outside the hexagon; rows r = -W..W follow in order, each preceded by
-// 2 to 4 zeros chosen so that plane position mod 3 equals the sublattice
-// (q - r) mod 3 of the column stored there; a second zero zone closes the
-// plane and stands for the rows W+1, W+2.  Every neighbour of a column in
-// rows r-2..r+2 then sits at a fixed offset from the column's own position
-// -- position(q, r') = base(r') + q -- and inside the same plane.  P is a
+// Padded-row plane layouts of one tube layer (the FP arrays nu and deg).
+// A zero zone opens the plane and stands for the rows -W-2, -W-1 outside the
+// hexagon; rows r = -W..W follow in order, each preceded by at least 2
+// zeros and placed so that plane position mod 3 equals the sublattice
+// (q - r) mod 3 of the column stored there: a strip (positions 3s, 3s+1,
+// 3s+2) then holds sublattices 0, 1, 2.  A second zero zone closes the plane
+// and stands for the rows W+1, W+2.  Every neighbour of a column in rows
+// r-2..r+2 sits at a fixed offset from the column's own position --
+// position(q, r') = base(r') + q -- and inside the same plane.  P is a
 // multiple of 16, so that every plane of the FP32 array and of the byte
-// degree array starts on a 16-byte boundary (bulk copies).  Strips are
-// triples of positions 3s, 3s+1, 3s+2 (sublattice 0, 1, 2); zero positions
+// degree array starts on a 16-byte boundary (bulk copies).  Zero positions
 // have degree 0, so a strip may cover zeros and simply writes zeros there.
+//
+// Two variants:
+//   compact (resident solver): 2 to 4 zeros before each row, zones of W + 8;
+//   paired (streamed solver): in addition base(r) is even for every row, so
+//     every row offset is even and a strip pair (positions 6h .. 6h+5) reads
+//     its runs with aligned 64-bit loads, and no strip pair holds columns of
+//     two rows; zones of W + 20 hold every read of a strip pair, whose
+//     positions may run up to five past its row's ends.
 // Fills the layout of radius W into caller buffers (any may be null) and
 // returns P, s_begin, n_strips.  No allocation: usable from every entry point.
 void layout_fill(int W, int* P_out, int* s_begin_out, int* n_strips_out, int16_t* strip_row,
-                 int32_t* row_off, int32_t* ppos, int32_t* pcol) {
+                 int32_t* row_off, int32_t* ppos, int32_t* pcol, bool paired) {
   const int nr = 2 * W + 1;  // W <= 255: at most 511 rows
   int start[511];
   auto qlo = [W](int ri) { const int r = ri - W; return r < 0 ? -W - r : -W; };
   auto len = [W](int ri) { const int r = ri - W; return 2 * W + 1 - (r < 0 ? -r : r); };
-  const int Z = W + 8;
+  const int Z = paired ? W + 20 : W + 8;
   int pos = Z;  // top zone [0, Z)
   for (int ri = 0; ri < nr; ++ri) {
     const int r = ri - W;
     const int want = ((qlo(ri) - r) % 3 + 3) % 3;
     int x = pos + 2;
-    while (x % 3 != want) ++x;
+    if (paired && ri > 0) {  // a new strip pair for the row's first column
+      const int g = ((pos - 1) / 6 + 1) * 6;
+      x = x > g ? x : g;
+    }
+    while (x % 3 != want || (paired && ((x - qlo(ri)) & 1))) ++x;
     start[ri] = x;
     pos = x + len(ri);
   }
   const int zone = pos;                      // bottom zone [zone, zone + Z)
   const int P = (zone + Z + 15) & ~15;
-  // base(row) = position(q, row) - q, for rows -W-2 .. W+2 (index ri + 2)
+  // base(row) = position(q, row) - q, for rows -W-2 .. W+2 (index ri + 2).
+  // Compact: rows -W-2, -W-1 are read at q in [-3, W+4], rows W+1, W+2 at q
+  // in [-W-4, 3].  Paired: at q in [-8, W+8] and [-W-8, 9], with even bases.
   auto base = [&](int ri_ext) -> int {
-    if (ri_ext <= 1) return 3;                  // rows -W-2, -W-1: q in [-3, W+4]
-    if (ri_ext >= nr + 2) return zone + W + 4;  // rows W+1, W+2: q in [-W-4, 3]
+    if (ri_ext <= 1) return paired ? 8 : 3;
+    if (ri_ext >= nr + 2) return paired ? zone + W + 10 + ((zone + W) & 1) : zone + W + 4;
     return start[ri_ext - 2] - qlo(ri_ext - 2);
   };
   const int sb = start[0] / 3, se = (start[nr - 1] + len(nr - 1) + 2) / 3;
@@ -83,17 +97,21 @@ void layout_fill(int W, int* P_out, int* s_begin_out, int* n_strips_out, int16_t
   }
 }
 
-// Plane positions [lo, hi) that the strips [k0, k1) read in one plane, for
-// every chunk of `chunk` strips; returns the largest hi - lo (aligned to 16).
-int max_segment(int W, int chunk) {
-  const PlaneLayout L = make_layout(W);
+// Largest bulk-copy segment of a chunk of `pairs` strip pairs of the paired
+// layout: plane positions [lo, hi) its pairs read, lo rounded down and hi up
+// to 16 entries (16-byte aligned FP32 and byte copies).
+int max_pair_segment(int W, int pairs) {
+  const PlaneLayout L = make_layout(W, true);
+  const int s_end = L.s_begin + L.n_strips;
+  const int h_begin = L.s_begin >> 1, h_end = (s_end + 1) >> 1;
   int best = 0;
-  for (int k0 = 0; k0 < L.n_strips; k0 += chunk) {
-    const int k1 = std::min(k0 + chunk, L.n_strips);
+  for (int h0 = h_begin; h0 < h_end; h0 += pairs) {
+    const int h1 = std::min(h0 + pairs, h_end);
     int lo = 1 << 30, hi = -(1 << 30);
-    for (int k = k0; k < k1; ++k) {
+    for (int h = h0; h < h1; ++h) {
+      const int st = std::min(std::max(2 * h + 1, L.s_begin), s_end - 1);
       int sl, sh;
-      strip_span(3 * (L.s_begin + k), &L.row_off[4 * L.strip_row[k]], &sl, &sh);
+      pair_span(6 * h, &L.row_off[4 * L.strip_row[st - L.s_begin]], &sl, &sh);
       lo = std::min(lo, sl); hi = std::max(hi, sh);
     }
     lo &= ~15;
@@ -103,30 +121,47 @@ int max_segment(int W, int chunk) {
   return best;
 }
 
-PlaneLayout make_layout(int W) {
+PlaneLayout make_layout(int W, bool paired) {
   PlaneLayout L;
-  layout_fill(W, &L.P, &L.s_begin, &L.n_strips, nullptr, nullptr, nullptr, nullptr);
+  layout_fill(W, &L.P, &L.s_begin, &L.n_strips, nullptr, nullptr, nullptr, nullptr, paired);
   L.strip_row.resize(L.n_strips);
   L.row_off.resize((size_t)(2 * W + 1) * 4);
   L.ppos.resize(n_columns(W));
   L.pcol.resize(L.P);
   layout_fill(W, nullptr, nullptr, nullptr, L.strip_row.data(), L.row_off.data(), L.ppos.data(),
-              L.pcol.data());
+              L.pcol.data(), paired);
   return L;
 }
 
 namespace {
 
-struct Entry {
-  int32_t* nbr = nullptr;
-  int8_t* sigma = nullptr;
-  int A = 0;
+struct DevLayout {
   int P = 0, s_begin = 0, n_strips = 0;
   int16_t* strip_row = nullptr;
   int32_t* row_off = nullptr;
   int32_t* ppos = nullptr;
   int32_t* pcol = nullptr;
 };
+
+struct Entry {
+  int32_t* nbr = nullptr;
+  int8_t* sigma = nullptr;
+  int A = 0;
+  DevLayout lay[2];  // compact (resident solver), paired (streamed solver)
+};
+
+pc_status upload_layout(const PlaneLayout& lay, DevLayout* d) {
+  d->P = lay.P; d->s_begin = lay.s_begin; d->n_strips = lay.n_strips;
+  PC_CUDA(cudaMalloc(&d->strip_row, sizeof(int16_t) * lay.strip_row.size()));
+  PC_CUDA(cudaMalloc(&d->row_off, sizeof(int32_t) * lay.row_off.size()));
+  PC_CUDA(cudaMalloc(&d->ppos, sizeof(int32_t) * lay.ppos.size()));
+  PC_CUDA(cudaMalloc(&d->pcol, sizeof(int32_t) * lay.pcol.size()));
+  PC_CUDA(cudaMemcpy(d->strip_row, lay.strip_row.data(), sizeof(int16_t) * lay.strip_row.size(), cudaMemcpyHostToDevice));
+  PC_CUDA(cudaMemcpy(d->row_off, lay.row_off.data(), sizeof(int32_t) * lay.row_off.size(), cudaMemcpyHostToDevice));
+  PC_CUDA(cudaMemcpy(d->ppos, lay.ppos.data(), sizeof(int32_t) * lay.ppos.size(), cudaMemcpyHostToDevice));
+  PC_CUDA(cudaMemcpy(d->pcol, lay.pcol.data(), sizeof(int32_t) * lay.pcol.size(), cudaMemcpyHostToDevice));
+  return PC_OK;
+}
 
 std::mutex g_mu;
 std::map<std::pair<int, int>, Entry> g_cache;  // (device, W) -> tables
@@ -169,16 +204,10 @@ pc_status get_lattice(int W, int L, Lattice* out) {
     }
     Entry e;
     e.A = A;
-    const PlaneLayout lay = make_layout(W);
-    e.P = lay.P; e.s_begin = lay.s_begin; e.n_strips = lay.n_strips;
-    PC_CUDA(cudaMalloc(&e.strip_row, sizeof(int16_t) * lay.strip_row.size()));
-    PC_CUDA(cudaMalloc(&e.row_off, sizeof(int32_t) * lay.row_off.size()));
-    PC_CUDA(cudaMalloc(&e.ppos, sizeof(int32_t) * lay.ppos.size()));
-    PC_CUDA(cudaMalloc(&e.pcol, sizeof(int32_t) * lay.pcol.size()));
-    PC_CUDA(cudaMemcpy(e.strip_row, lay.strip_row.data(), sizeof(int16_t) * lay.strip_row.size(), cudaMemcpyHostToDevice));
-    PC_CUDA(cudaMemcpy(e.row_off, lay.row_off.data(), sizeof(int32_t) * lay.row_off.size(), cudaMemcpyHostToDevice));
-    PC_CUDA(cudaMemcpy(e.ppos, lay.ppos.data(), sizeof(int32_t) * lay.ppos.size(), cudaMemcpyHostToDevice));
-    PC_CUDA(cudaMemcpy(e.pcol, lay.pcol.data(), sizeof(int32_t) * lay.pcol.size(), cudaMemcpyHostToDevice));
+    for (int v = 0; v < 2; ++v) {
+      const pc_status rc = upload_layout(make_layout(W, v == 1), &e.lay[v]);
+      if (rc) return rc;
+    }
     PC_CUDA(cudaMalloc(&e.nbr, nbr.size() * sizeof(int32_t)));
     PC_CUDA(cudaMalloc(&e.sigma, sig.size()));
     PC_CUDA(cudaMemcpy(e.nbr, nbr.data(), nbr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -195,8 +224,12 @@ pc_status get_lattice(int W, int L, Lattice* out) {
   out->TWP = out->TW + 2;
   out->nbr = e.nbr;
   out->sigma = e.sigma;
-  out->P = e.P; out->s_begin = e.s_begin; out->n_strips = e.n_strips;
-  out->strip_row = e.strip_row; out->row_off = e.row_off; out->ppos = e.ppos; out->pcol = e.pcol;
+  const DevLayout& c = e.lay[0];
+  const DevLayout& d = e.lay[1];
+  out->P = c.P; out->s_begin = c.s_begin; out->n_strips = c.n_strips;
+  out->strip_row = c.strip_row; out->row_off = c.row_off; out->ppos = c.ppos; out->pcol = c.pcol;
+  out->P2 = d.P; out->s_begin2 = d.s_begin; out->n_strips2 = d.n_strips;
+  out->strip_row2 = d.strip_row; out->row_off2 = d.row_off; out->ppos2 = d.ppos; out->pcol2 = d.pcol;
   return PC_OK;
 }
 
@@ -208,10 +241,12 @@ void release_lattices() {
     cudaSetDevice(kv.first.first);
     cudaFree(kv.second.nbr);
     cudaFree(kv.second.sigma);
-    cudaFree(kv.second.strip_row);
-    cudaFree(kv.second.row_off);
-    cudaFree(kv.second.ppos);
-    cudaFree(kv.second.pcol);
+    for (const DevLayout& d : kv.second.lay) {
+      cudaFree(d.strip_row);
+      cudaFree(d.row_off);
+      cudaFree(d.ppos);
+      cudaFree(d.pcol);
+    }
   }
   cudaSetDevice(cur);
   g_cache.clear();
@@ -219,12 +254,11 @@ void release_lattices() {
 
 }  // namespace pc
 
-// Host-side copy of the plane layout of radius W (diagnostics and tests).
-extern "C" pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
-                                       int16_t* strip_row, int32_t* row_off, int32_t* ppos,
-                                       int32_t* pcol) {
-  if (W < 0 || W > 255) { pc::set_error("pc_lattice_layout: W must be in [0, 255]"); return PC_ERR_ARG; }
-  const pc::PlaneLayout L = pc::make_layout(W);
+namespace {
+pc_status copy_layout(int32_t W, bool paired, int32_t* P, int32_t* s_begin, int32_t* n_strips,
+                      int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol) {
+  if (W < 0 || W > 255) { pc::set_error("layout: W must be in [0, 255]"); return PC_ERR_ARG; }
+  const pc::PlaneLayout L = pc::make_layout(W, paired);
   if (P) *P = L.P;
   if (s_begin) *s_begin = L.s_begin;
   if (n_strips) *n_strips = L.n_strips;
@@ -233,4 +267,18 @@ extern "C" pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, 
   if (ppos) std::copy(L.ppos.begin(), L.ppos.end(), ppos);
   if (pcol) std::copy(L.pcol.begin(), L.pcol.end(), pcol);
   return PC_OK;
+}
+}  // namespace
+
+// Host-side copies of the plane layouts of radius W (diagnostics and tests).
+extern "C" pc_status pc_lattice_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
+                                       int16_t* strip_row, int32_t* row_off, int32_t* ppos,
+                                       int32_t* pcol) {
+  return copy_layout(W, false, P, s_begin, n_strips, strip_row, row_off, ppos, pcol);
+}
+
+extern "C" pc_status pc_stream_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_strips,
+                                      int16_t* strip_row, int32_t* row_off, int32_t* ppos,
+                                      int32_t* pcol) {
+  return copy_layout(W, true, P, s_begin, n_strips, strip_row, row_off, ppos, pcol);
 }

@@ -114,10 +114,14 @@ struct Ctx {
 };
 
 
-// items along the plane / column axis of one unit row, per kind: strips for
-// FP, plane positions for PREP and CLEAN, columns for BITS and DRAW
+// items along the plane / column axis of one unit row, per kind: strip pairs
+// for FP, plane positions for PREP and CLEAN, columns for BITS and DRAW
 __host__ __device__ inline int width_of(int kind, const Lattice& lat) {
-  return kind == U_FP ? lat.n_strips : (kind == U_PREP || kind == U_CLEAN) ? lat.P : lat.A;
+  if (kind == U_FP) {  // strip pairs of the paired layout
+    const int s_end = lat.s_begin + lat.n_strips;
+    return ((s_end + 1) >> 1) - (lat.s_begin >> 1);
+  }
+  return (kind == U_PREP || kind == U_CLEAN) ? lat.P : lat.A;
 }
 
 __host__ __device__ inline int units_of(int kind, int lo, int hi, const Lattice& lat) {
@@ -280,8 +284,8 @@ __device__ __forceinline__ void ring_next(int& slot, uint32_t& par, int nring) {
   if (++slot == nring) { slot = 0; par ^= 1u; }
 }
 
-// One FP unit: strips [k0, k0 + kCols) (one per thread) over layers
-// [t0, t1).  Layer t reads planes t+2, t+3 of nu and layer t of the degrees
+// One FP unit: strip pairs [k0, k0 + kCols) (one per thread, 6 plane
+// positions each) over layers [t0, t1).  Layer t reads planes t+2, t+3 of nu and layer t of the degrees
 // (planes t+1 and older are already in registers).  The segment [lo, hi) of
 // each plane the chunk touches, and the same byte range of the degree layer
 // three planes below it, are copied into the next ring slot (cp.async.bulk;
@@ -299,16 +303,20 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
                                                int* s_red) {
   const int tid = threadIdx.x, P = lat.P, cap = x.seg_cap, nring = x.nring;
   const int warp = tid >> 5;
-  // threads past the last strip repeat it: they write the same values to
-  // the same addresses, and the layer loop needs no per-thread branch
-  const int k = min(k0 + tid, lat.n_strips - 1);
+  // strip pair h = positions 6h .. 6h+5 (paired layout: one row, even row
+  // offsets); threads past the last pair repeat it: they write the same
+  // values to the same addresses, and the layer loop needs no branch
+  const int s_end = lat.s_begin + lat.n_strips;
+  const int h_begin = lat.s_begin >> 1, h_end = (s_end + 1) >> 1;
+  const int h = min(h_begin + k0 + tid, h_end - 1);
+  const int st = min(max(2 * h + 1, lat.s_begin), s_end - 1);  // a strip of the pair holding its row
   int lo, hi;
-  const int b = 3 * (lat.s_begin + k);
-  const int32_t* ro = lat.row_off + 4 * lat.strip_row[k];
+  const int b = 6 * h;
+  const int32_t* ro = lat.row_off + 4 * lat.strip_row[st - lat.s_begin];
   const int r0 = __ldg(ro), r1 = __ldg(ro + 1), r2 = __ldg(ro + 2), r3 = __ldg(ro + 3);
   {
     const int32_t rr[4] = {r0, r1, r2, r3};
-    strip_span(b, rr, &lo, &hi);
+    pair_span(b, rr, &lo, &hi);
   }
   // segment of the chunk: block min / max
 #pragma unroll
@@ -363,8 +371,11 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     }
     return sl;
   };
-  const int u0 = b - 2 + r2 - lo_al, d0 = b - 1 + r1 - lo_al, c0 = b - 1 - lo_al;
-  const int e0 = b - 1 + r3 - lo_al, f0 = b + 1 + r0 - lo_al, g0 = b - lo_al;
+  // shared byte offsets within a slot of this pair's 64-bit-aligned reads:
+  // rows r+1, r-1, r, r+2 from position b - 2, row r-2 from b; degrees at b
+  const uint32_t ou = 4u * (uint32_t)(b - 2 + r2 - lo_al), od = 4u * (uint32_t)(b - 2 + r1 - lo_al);
+  const uint32_t oc = 4u * (uint32_t)(b - 2 - lo_al), oe = 4u * (uint32_t)(b - 2 + r3 - lo_al);
+  const uint32_t of = 4u * (uint32_t)(b + r0 - lo_al), og = (uint32_t)(b - lo_al);
   // shared addresses (bytes): slot s of the FP32 ring at ring_s + s * cap4,
   // of the degree ring at dring_s + s * cap
   const uint32_t ring_s = smem_u32(ring), dring_s = smem_u32(dring), inv_s = smem_u32(inv);
@@ -373,15 +384,18 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   for (int i = 0; i < nring; ++i) issue();
   const int s1 = consume();  // plane t0 + 1
   const int s2 = consume();  // plane t0 + 2
-  float up2, dp2, cp[4];
-  Runs A, B;
+  // layer t-1 values of the pair: U[2], D[2] of each strip, C[0..6]
+  float pu[2], pd[2], pcv[7];
+  PairRuns A, B;
   {
+    PairRuns T;
     const uint32_t p1 = ring_s + (uint32_t)s1 * cap4;
-    up2 = lds_f<8>(p1 + 4u * (uint32_t)u0); dp2 = lds_f<8>(p1 + 4u * (uint32_t)d0);
-    const uint32_t c1 = p1 + 4u * (uint32_t)c0;
-    cp[0] = lds_f<0>(c1); cp[1] = lds_f<4>(c1); cp[2] = lds_f<8>(c1); cp[3] = lds_f<12>(c1);
+    load_pair_runs(T, p1 + ou, p1 + od, p1 + oc);
+    pu[0] = T.u[2]; pu[1] = T.u[5]; pd[0] = T.d[2]; pd[1] = T.d[5];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) pcv[i] = T.c[i];
     const uint32_t q2 = ring_s + (uint32_t)s2 * cap4;
-    load_runs_s(A, q2 + 4u * (uint32_t)u0, q2 + 4u * (uint32_t)d0, q2 + 4u * (uint32_t)c0);
+    load_pair_runs(A, q2 + ou, q2 + od, q2 + oc);
   }
   __syncthreads();  // plane t0 + 1's slot is free
   issue();
@@ -395,12 +409,11 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     {
       const int s3 = consume();  // plane t + 3
       const uint32_t p3 = ring_s + (uint32_t)s3 * cap4;
-      load_runs_s(B, p3 + 4u * (uint32_t)u0, p3 + 4u * (uint32_t)d0, p3 + 4u * (uint32_t)c0);
-      strip_emit_s(A, B, up2, dp2, cp, p2 + 4u * (uint32_t)e0, p2 + 4u * (uint32_t)f0,
-                   dring_s + (uint32_t)s3 * (uint32_t)cap + (uint32_t)g0, inv_s, out);
-      up2 = A.U[2]; dp2 = A.D[2];
+      load_pair_runs(B, p3 + ou, p3 + od, p3 + oc);
+      pair_emit(A, B, pu, pd, pcv, p2 + oe, p2 + of, dring_s + (uint32_t)s3 * (uint32_t)cap + og, inv_s, out);
+      pu[0] = A.u[2]; pu[1] = A.u[5]; pd[0] = A.d[2]; pd[1] = A.d[5];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) cp[i] = A.C[i];
+      for (int i = 0; i < 7; ++i) pcv[i] = A.c[i];
       p2 = p3;
       out += P;
     }
@@ -412,12 +425,11 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
     {
       const int s3 = consume();
       const uint32_t p3 = ring_s + (uint32_t)s3 * cap4;
-      load_runs_s(A, p3 + 4u * (uint32_t)u0, p3 + 4u * (uint32_t)d0, p3 + 4u * (uint32_t)c0);
-      strip_emit_s(B, A, up2, dp2, cp, p2 + 4u * (uint32_t)e0, p2 + 4u * (uint32_t)f0,
-                   dring_s + (uint32_t)s3 * (uint32_t)cap + (uint32_t)g0, inv_s, out);
-      up2 = B.U[2]; dp2 = B.D[2];
+      load_pair_runs(A, p3 + ou, p3 + od, p3 + oc);
+      pair_emit(B, A, pu, pd, pcv, p2 + oe, p2 + of, dring_s + (uint32_t)s3 * (uint32_t)cap + og, inv_s, out);
+      pu[0] = B.u[2]; pu[1] = B.u[5]; pd[0] = B.d[2]; pd[1] = B.d[5];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) cp[i] = B.C[i];
+      for (int i = 0; i < 7; ++i) pcv[i] = B.c[i];
       p2 = p3;
       out += P;
     }
@@ -428,7 +440,7 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   }
 }
 
-__global__ void __launch_bounds__(kCols, 3) sweep_kernel(Ctx x) {
+__global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
   // x.nring slots of x.seg_cap floats (nu planes), then x.nring of x.seg_cap bytes (degrees)
   extern __shared__ __align__(128) float ring[];
   uint8_t* dring = reinterpret_cast<uint8_t*>(ring + (size_t)x.nring * x.seg_cap);
@@ -771,7 +783,7 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
 
 size_t stream_slot_bytes(int W, int L) {
   int P = 0;
-  layout_fill(W, &P, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  layout_fill(W, &P, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, true);
   return slot_bytes_of((int)n_columns(W), L, P);
 }
 
@@ -789,11 +801,11 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   unsigned long long max_steps = 0;
   std::vector<QDev> h(nq);
   for (int i = 0; i < nq; ++i) {
-    h[i].lat = qs[i].lat; h[i].occ = qs[i].occ; h[i].occ_bits = qs[i].occ_bits;
+    h[i].lat = stream_view(qs[i].lat); h[i].occ = qs[i].occ; h[i].occ_bits = qs[i].occ_bits;
     h[i].words_per_cfg = qs[i].words_per_cfg; h[i].n_cfg = qs[i].n_cfg; h[i].cfg0 = qs[i].cfg0;
     h[i].out = qs[i].out; h[i].item0 = n_items; h[i].bits_only = qs[i].bits_only;
     n_items += qs[i].n_cfg;
-    slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L, qs[i].lat.P));
+    slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L, qs[i].lat.P2));
     max_steps = std::max<unsigned long long>(max_steps, (unsigned long long)qs[i].lat.N + 4);
   }
   size_t free_b = 0, total_b = 0;
@@ -833,7 +845,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   x.use_cond = 0; x.server = 0; x.slot_base = nullptr; x.qnext = nullptr; x.qdone = nullptr;
   {
     int cap = 16;
-    for (int i = 0; i < nq; ++i) cap = std::max(cap, max_segment(qs[i].lat.W, kCols) + 16);
+    for (int i = 0; i < nq; ++i) cap = std::max(cap, max_pair_segment(qs[i].lat.W, kCols) + 16);
     x.seg_cap = cap;
     x.nring = ring_depth(cap);
     const int bytes = sweep_smem_bytes(cap, x.nring);
@@ -993,7 +1005,7 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
   x.next_unit = x.ticks + 3;
   x.pool = nullptr; x.slot_bytes = 0; x.max_ticks = 0xffffffffu;
   x.use_cond = 0; x.server = 1;
-  x.seg_cap = max_segment(max_W, kCols) + 16;  // any lattice the server accepts
+  x.seg_cap = max_pair_segment(max_W, kCols) + 16;  // any lattice the server accepts
   x.nring = ring_depth(x.seg_cap);
   E->max_queries = nq;
   pc_status rc = PC_OK;
@@ -1057,7 +1069,7 @@ pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& sq
   QChunk ch;
   ch.base = qi; ch.n = 1;
   QDev& d = ch.q[0];
-  d.lat = sq.lat; d.occ = sq.occ; d.occ_bits = sq.occ_bits; d.words_per_cfg = sq.words_per_cfg;
+  d.lat = stream_view(sq.lat); d.occ = sq.occ; d.occ_bits = sq.occ_bits; d.words_per_cfg = sq.words_per_cfg;
   d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0; d.bits_only = sq.bits_only;
   upload_queries_kernel<<<1, kQChunk, 0, st>>>((QDev*)E->x.qs, ch);
   PC_CUDA(cudaGetLastError());

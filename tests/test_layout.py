@@ -67,6 +67,52 @@ def test_strip_gathers_hit_the_right_neighbours(W):
                 assert got == want, (W, st, j, d, got, want)
 
 
+# strip-pair runs of the streamed solver: (name, start relative to 6h (plus
+# the row offset), rows delta, 64-bit loads)
+PAIR_RUNS = {"U": (-2, +1, 5), "D": (-2, -1, 5), "C": (-2, 0, 5), "E": (-2, +2, 4), "F": (0, -2, 4)}
+
+
+@pytest.mark.parametrize("W", [0, 1, 2, 3, 4, 7, 8, 16, 33, 64, 100])
+def test_strip_pair_layout_of_the_streamed_solver(W):
+    """The paired layout: even row offsets (aligned 64-bit loads), no strip
+    pair holding columns of two rows, every 64-bit read of every pair inside
+    the plane, and every site of a pair reading its true neighbours through
+    its strip's runs at the pair's row offsets."""
+    lay = pc.pc_stream_layout(W)
+    P, ppos, pcol = lay["P"], lay["ppos"], lay["pcol"]
+    sb, ns = lay["s_begin"], lay["n_strips"]
+    q, r, s = oracle.columns(W)
+    A = len(q)
+    assert P % 16 == 0
+    assert np.array_equal(pcol[ppos], np.arange(A)) and (pcol >= 0).sum() == A
+    assert np.all(ppos % 3 == (q - r) % 3)
+    assert np.all(lay["row_off"] % 2 == 0)
+    idx = {(int(q[a]), int(r[a])): a for a in range(A)}
+    h_begin, h_end = sb // 2, (sb + ns + 1) // 2
+    for h in range(h_begin, h_end):
+        b = 6 * h
+        rows = {int(r[a]) for a in pcol[b:b + 6] if a >= 0}
+        assert len(rows) <= 1, (W, h, rows)
+        st = min(max(2 * h + 1, sb), sb + ns - 1)
+        ri = int(lay["strip_row"][st - sb])
+        if rows:
+            assert rows == {ri - W}, (W, h, rows, ri)
+        off = {0: 0, **{d: int(lay["row_off"][ri, ROW_K[d]]) for d in (-2, -1, 1, 2)}}
+        for name, (c, dr, nload) in PAIR_RUNS.items():
+            start = b + c + off[dr]
+            assert start % 2 == 0 and 0 <= start and start + 2 * nload <= P, (W, h, name)
+        for j in range(6):  # every site of the pair, through its strip's runs
+            a = pcol[b + j]
+            if a < 0:
+                continue
+            bs = b + 3 * (j // 3)
+            starts = {name: bs + cc + off[dr] for name, (cc, dr) in RUNS.items()}
+            for d, (dq, dr, name, kk) in DIRS.items():
+                got = pcol[starts[name] + j % 3 + kk]
+                want = idx.get((int(q[a]) + dq, int(r[a]) + dr), -1)
+                assert got == want, (W, h, j, d, got, want)
+
+
 def test_static_entry_point_tables_cover_its_widest_lattice():
     # pc_inspect_static keeps the layout of every accepted width (W <= 51) in
     # fixed tables of 9216 plane entries and 9216 / 3 + 2 strips
