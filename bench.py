@@ -277,9 +277,10 @@ HBM_BYTES_PER_SU = 8.375
 # DRAM bytes (read + write) measured with ncu on the current kernels, to be
 # re-measured whenever they change: the resident kernel per p-sweep launch
 # (tables and outputs only), and the streamed sweep per site-update
-# (controlled capture of the large lattice with 4 active slots)
-RESIDENT_DRAM_BYTES_PER_LAUNCH = 155160.0
-SWEEP_DRAM_BYTES_PER_SU = (266.19e6 + 267.03e6) / (29.95e6 + 30.00e6)
+# (controlled capture of the large lattice with 4 active slots, tick 600:
+# 4 x 12,481 columns x 600 layers)
+RESIDENT_DRAM_BYTES_PER_LAUNCH = 81152.0  # p = 0.2, 2,000 configurations
+SWEEP_DRAM_BYTES_PER_SU = (173.08e6 + 97.65e6) / 29.95e6
 # bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
 BITS_BYTES_PER_SU = 0.375
 
