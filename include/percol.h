@@ -182,15 +182,20 @@ typedef struct pc_result {
 
 /*
  * Inspect many queries of mixed lattice sizes in one GPU submission (the
- * batching of a finite-size-scaling sweep, Sec. III): every query whose
- * configuration state fits one CTA's shared memory runs the resident solver
- * (one persistent kernel per query, all concurrent), every other query shares
- * one pool of streamed-solver slots that refill as configurations finish; the
- * whole batch is one CUDA graph, built on the first call and replayed when
- * the same batch (same queries and output pointers) is submitted again.  The
+ * batching of a finite-size-scaling sweep, Sec. III): the queries whose
+ * configuration state fits one CTA's shared memory run the resident solver
+ * in at most three persistent launches, one per shared-memory class (up to
+ * a quarter, a half, or all of an SM's shared memory), each taking the
+ * configurations of its queries from one list ordered by decreasing lattice
+ * size; every other query shares one pool of streamed-solver slots that
+ * refill as configurations finish, largest lattices first.  The whole batch
+ * is one CUDA graph, built on the first call and replayed when the same
+ * batch (same queries and output pointers) is submitted again.  The
  * resident CTA size of each (W, L, p bin of width 0.025) is picked by timing
  * candidates on first use (autotuner; choices kept in memory and in the JSON
- * file named by the environment variable PC_TUNE_FILE, if set).
+ * file named by the environment variable PC_TUNE_FILE, if set); a launch
+ * runs with the size tuned for its heaviest query (sites x configurations),
+ * reported in pc_result.threads.
  * out: [n_queries] host summaries, or NULL.  Unless flags has PC_ASYNC the
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY

@@ -2,10 +2,12 @@
 // lattice sizes) and the autotuner of the resident solver's CTA size.
 //
 // A batch becomes one CUDA graph:
-//   memset(counters) -> { resident kernel of query i, for every query whose
-//                         state fits shared memory (parallel graph branches,
-//                         so their persistent grids overlap and fill each
-//                         other's tails) }
+//   memset(counters) -> { at most three persistent resident launches, one per
+//                         shared-memory class, over every query whose state
+//                         fits shared memory, configurations taken from one
+//                         list in decreasing lattice size (parallel graph
+//                         branches, so the grids overlap and fill each other's
+//                         tails) }
 //                    -> { init -> WHILE(sweep, control) of the streamed solver
 //                         over all remaining queries, sharing one slot pool }
 // The instantiated graph and its device memory are cached per batch (same
@@ -136,6 +138,7 @@ struct BatchGraph {
   int device = 0;
   char* mem = nullptr;       // counters + host-output staging
   size_t mem_bytes = 0;
+  char* tab = nullptr;       // query tables of the persistent resident launches
   StreamPlan* plan = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -168,6 +171,7 @@ void destroy_batch(BatchGraph* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->plan) stream_plan_release(b->plan, 0);
   if (b->mem) cudaFree(b->mem);
+  if (b->tab) cudaFree(b->tab);
   cudaDeviceSynchronize();
   cudaSetDevice(cur);
   delete b;
@@ -180,13 +184,76 @@ std::string batch_key(const pc_query* q, int64_t n, int32_t flags, int dev) {
   return k;
 }
 
+// A resident-size query of a batch: its arguments, index, autotuned CTA
+// size and shared memory.
+struct ResidentQuery {
+  ResidentArgs a;
+  int64_t index;
+  int threads;
+  size_t smem;
+};
+
+// The batch's resident-size queries as at most three persistent launches,
+// one per shared-memory class (up to 1/4, 1/2 and all of an SM's shared
+// memory: 4+, 2-3 and 1 CTA per SM), so that small lattices keep their
+// occupancy.  Within a launch the queries are ordered by decreasing lattice
+// size (sites), so the longest configurations start first and the shorter
+// ones fill the tails; the CTA size is the autotuned one of the launch's
+// heaviest query (sites x configurations).  work: 3 zeroed counters.
+pc_status add_resident_launches(BatchGraph* b, std::vector<ResidentQuery>& rq, const pc_query* q,
+                                unsigned long long* work, const cudaGraphNode_t* dep) {
+  int dev = 0, smem_sm = 0;
+  PC_CUDA(cudaGetDevice(&dev));
+  PC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  auto cls = [&](size_t sm) { return sm * 4 <= (size_t)smem_sm ? 0 : sm * 2 <= (size_t)smem_sm ? 1 : 2; };
+  std::stable_sort(rq.begin(), rq.end(), [](const ResidentQuery& x, const ResidentQuery& y) {
+    return x.a.lat.N > y.a.lat.N;
+  });
+  // device tables: per class ResidentArgs[] and item offsets[] (one allocation)
+  const size_t n = rq.size();
+  const size_t args_b = (sizeof(ResidentArgs) * n + 255) & ~(size_t)255;
+  const size_t off_b = (sizeof(long long) * (n + 3) + 255) & ~(size_t)255;
+  PC_CUDA(cudaMalloc((void**)&b->tab, 3 * (args_b + off_b)));
+  for (int c = 0; c < 3; ++c) {
+    std::vector<ResidentArgs> args;
+    std::vector<long long> item0{0};
+    size_t smem = 0;
+    int threads = 0;
+    double heavy = -1.0;
+    for (const ResidentQuery& r : rq) {
+      if (cls(r.smem) != c) continue;
+      args.push_back(r.a);
+      item0.push_back(item0.back() + r.a.n_cfg);
+      smem = std::max(smem, r.smem);
+      const double w = (double)r.a.lat.N * (double)r.a.n_cfg;
+      if (w > heavy) { heavy = w; threads = r.threads; }
+    }
+    if (args.empty() || item0.back() == 0) continue;
+    for (const ResidentQuery& r : rq)
+      if (cls(r.smem) == c) b->qp[r.index].threads = threads;
+    char* at = b->tab + c * (args_b + off_b);
+    PC_CUDA(cudaMemcpy(at, args.data(), sizeof(ResidentArgs) * args.size(), cudaMemcpyHostToDevice));
+    PC_CUDA(cudaMemcpy(at + args_b, item0.data(), sizeof(long long) * item0.size(), cudaMemcpyHostToDevice));
+    ResidentBatch rb;
+    rb.qs = (const ResidentArgs*)at;
+    rb.item0 = (const long long*)(at + args_b);
+    rb.nq = (int)args.size();
+    rb.work = work + c;
+    cudaGraphNode_t node;
+    pc_status rc = resident_multi_add_node(rb, item0.back(), smem, threads, b->graph, dep, 1, &node);
+    if (rc) return rc;
+  }
+  return PC_OK;
+}
+
 pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t st, BatchGraph** out) {
   const bool dev_out = (flags & PC_OUT_DEVICE) != 0;
   BatchGraph* b = new BatchGraph();
   cudaGetDevice(&b->device);
   b->qp.resize(nq);
-  // device memory: per query 2 counters (+ staging of host outputs)
-  size_t bytes = 256 + (size_t)nq * 16;
+  // device memory: per query 2 counters, 3 class counters (+ staging of
+  // host outputs)
+  size_t bytes = 256 + (size_t)nq * 16 + 64;
   if (!dev_out)
     for (int64_t i = 0; i < nq; ++i) bytes += ((size_t)q[i].n_configs * 13 + 256) & ~(size_t)255;
   b->mem_bytes = bytes;
@@ -198,12 +265,13 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
   }
   pc_status rc = PC_OK;
   std::vector<StreamQuery> sq;
+  std::vector<ResidentQuery> rq;
   do {
     unsigned long long* ctr = (unsigned long long*)b->mem;  // [nq][2]: n_perc, work
-    char* stage = b->mem + 256 + (size_t)nq * 16;
+    char* stage = b->mem + 256 + (size_t)nq * 16 + 64;
     if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess) { rc = cuda_fail(e, "graph create"); break; }
     cudaMemsetParams mp = {};
-    mp.dst = b->mem; mp.value = 0; mp.elementSize = 1; mp.width = 256 + (size_t)nq * 16; mp.height = 1;
+    mp.dst = b->mem; mp.value = 0; mp.elementSize = 1; mp.width = 256 + (size_t)nq * 16 + 64; mp.height = 1;
     mp.pitch = 0;
     cudaGraphNode_t n_zero;
     if ((e = cudaGraphAddMemsetNode(&n_zero, b->graph, nullptr, 0, &mp)) != cudaSuccess) { rc = cuda_fail(e, "memset node"); break; }
@@ -226,7 +294,6 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
       os.cfg = 0; os.wl = (uint32_t)q[i].W | ((uint32_t)q[i].L << 8); os.T = threshold_of(q[i].p);
       if (resident_fits(q[i].W, q[i].L)) {
         P.solver = 0;
-        P.threads = tuned_threads(lat, q[i].p, q[i].seed, st);
         ResidentArgs a;
         a.lat = lat; a.occ = os; a.occ_bits = nullptr; a.words_per_cfg = (lat.N + 31) / 32;
         a.n_cfg = q[i].n_configs; a.cfg0 = (uint32_t)q[i].config_begin;
@@ -235,8 +302,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         a.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
         a.verdict_first = (flags & PC_VERDICT_FIRST) ? 1 : 0;
         if (!a.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
-        cudaGraphNode_t node;
-        rc = resident_add_node(a, P.threads, b->graph, &n_zero, 1, &node);
+        rq.push_back({a, i, tuned_threads(lat, q[i].p, q[i].seed, st), resident_smem(lat)});
       } else {
         P.solver = 1;
         StreamQuery s;
@@ -250,6 +316,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
       }
     }
     if (rc) break;
+    if (!rq.empty() && (rc = add_resident_launches(b, rq, q, ctr + 2 * nq, &n_zero)) != PC_OK) break;
     if (!sq.empty()) {
       // largest lattices first: long configurations start early
       std::stable_sort(sq.begin(), sq.end(), [](const StreamQuery& x, const StreamQuery& y) {

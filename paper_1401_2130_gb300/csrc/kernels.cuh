@@ -33,10 +33,25 @@ struct ResidentArgs {
   int verdict_first = 0;     // reached set first, FP32 recursion only where it percolates
 };
 constexpr int kResidentMaxThreads = 640;  // resident CTA size limit: 20 warps at <= 96 registers
+// Several queries in one persistent resident launch (device pointers): the
+// configurations of query q are the items [item0[q], item0[q + 1]) of one
+// list, counted by *work (zeroed).  Every query's own work field is unused.
+struct ResidentBatch {
+  const ResidentArgs* qs;   // [nq]
+  const long long* item0;   // [nq + 1]
+  int nq;
+  unsigned long long* work;
+};
 size_t resident_smem(const Lattice& lat);
 pc_status launch_resident(const ResidentArgs& args, int threads, cudaStream_t st);
 pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g,
                             const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* out);
+// One persistent launch over several queries (graph node): dynamic shared
+// memory smem (the largest query's), grid = CTAs that fit x SMs, capped at
+// the item count.
+pc_status resident_multi_add_node(const ResidentBatch& b, long long n_items, size_t smem, int threads,
+                                  cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                                  cudaGraphNode_t* out);
 // default CTA size of the resident solver (about 16 tube layers per thread)
 int resident_threads(int A, int L);
 // CTA size picked by the autotuner for (W, L, p bin) (batch.cu); times

@@ -241,16 +241,24 @@ __device__ __forceinline__ void prepare_layers(const Smem& sm, const Lattice& la
 
 size_t resident_smem(const Lattice& lat) { return smem_bytes(lat.W, lat.A, lat.L, lat.P, lat.n_strips); }
 
-__global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs Pa) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Lattice& lat = Pa.lat;
-  const int W = lat.W, A = lat.A, L = lat.L, S = lat.S, TWP = lat.TWP, P = lat.P;
-  const int NS = lat.n_strips, SB = lat.s_begin;
-  const int tid = threadIdx.x, T = blockDim.x;
-  Smem sm = carve(smem_raw, W, A, L, P, NS);
+// Per-query state of a CTA: the shared-memory carve of the query's lattice
+// and, when the CTA has a thread per column, that thread's column tables.
+struct QueryState {
+  Smem sm;
+  bool own_col;
+  uint32_t my_nb[kLateral / 2];  // packed int16 pairs of neighbour columns
+  int my_sg;
+};
 
-  // tables into shared memory (resident lattices have A < 2^15: int16 columns);
-  // zero the guard and boundary planes of nu
+// Loads the lattice tables of query Pa into shared memory (resident
+// lattices have A < 2^15: int16 columns) and zeroes the guard and boundary
+// planes of nu.  Block-uniform.
+__device__ __forceinline__ void setup_query(const ResidentArgs& Pa, unsigned char* smem_raw, QueryState& qs) {
+  const Lattice& lat = Pa.lat;
+  const int W = lat.W, A = lat.A, L = lat.L, P = lat.P, NS = lat.n_strips;
+  const int tid = threadIdx.x, T = blockDim.x;
+  qs.sm = carve(smem_raw, W, A, L, P, NS);
+  const Smem& sm = qs.sm;
   for (int k = tid; k < A * kLateral; k += T) sm.nbr[k] = (int16_t)lat.nbr[k];
   for (int k = tid; k < A; k += T) sm.sig[k] = lat.sigma[k];
   for (int k = tid; k < NS; k += T) sm.srow[k] = lat.strip_row[k];
@@ -261,7 +269,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
     sm.nu[0][(size_t)(L + 2) * P + k] = 0.f; sm.nu[1][(size_t)(L + 2) * P + k] = 0.f;
   }
   __syncthreads();
+  // a thread per column owns the column's reached-set words and keeps its
+  // neighbour table
+  qs.own_col = T >= A && tid < A;
+  qs.my_sg = 0;
+  if (qs.own_col) {
+    qs.my_sg = sm.sig[tid];
+#pragma unroll
+    for (int d = 0; d < kLateral; d += 2)
+      qs.my_nb[d >> 1] = (uint32_t)(uint16_t)sm.nbr[tid * kLateral + d] |
+                         ((uint32_t)(uint16_t)sm.nbr[tid * kLateral + d + 1] << 16);
+  }
+}
 
+// Inspects configuration rel of query Pa, whose tables setup_query loaded.
+// Block-uniform; ends with a block barrier.
+__device__ __forceinline__ void solve_config(const ResidentArgs& Pa, const QueryState& qst, long long rel) {
+  const Lattice& lat = Pa.lat;
+  const int A = lat.A, L = lat.L, S = lat.S, TWP = lat.TWP, P = lat.P;
+  const int NS = lat.n_strips, SB = lat.s_begin;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const Smem& sm = qst.sm;
+  const bool own_col = qst.own_col;
+  const int my_sg = qst.my_sg;
+  const uint32_t (&my_nb)[kLateral / 2] = qst.my_nb;
   const int CH = Pa.prep_chunk;
   const bool bits_only = Pa.bits_only != 0;
   // verdict first: the reached set alone decides every configuration, and
@@ -270,24 +301,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
   const bool vfirst = Pa.verdict_first != 0 && !bits_only && L > 1;
   const bool no_fp = bits_only || vfirst;  // no FP32 sweep in the first pass
   const int n_words_col = S * TWP;
-  // when the CTA has a thread per column, that thread owns the column's
-  // reached-set words and keeps its neighbour table (packed int16 pairs)
-  const bool own_col = T >= A && tid < A;
-  uint32_t my_nb[kLateral / 2];
-  int my_sg = 0;
-  if (own_col) {
-    my_sg = sm.sig[tid];
-#pragma unroll
-    for (int d = 0; d < kLateral; d += 2)
-      my_nb[d >> 1] = (uint32_t)(uint16_t)sm.nbr[tid * kLateral + d] |
-                      ((uint32_t)(uint16_t)sm.nbr[tid * kLateral + d + 1] << 16);
-  }
-
-  for (;;) {
-    if (tid == 0) sm.scal[0] = (long long)atomicAdd(Pa.work, 1ull);
-    __syncthreads();
-    const long long rel = sm.scal[0];
-    if (rel >= Pa.n_cfg) break;
+  {
     const uint32_t cfg = Pa.cfg0 + (uint32_t)rel;
 
     // reset bit arrays and flags
@@ -438,6 +452,52 @@ __global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs P
   }
 }
 
+// One query: every CTA takes configurations from the query's counter.
+__global__ void __launch_bounds__(kMaxThreads, 1) resident_kernel(ResidentArgs Pa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_item;
+  QueryState qs;
+  setup_query(Pa, smem_raw, qs);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(Pa.work, 1ull);
+    __syncthreads();
+    const long long rel = s_item;
+    if (rel >= Pa.n_cfg) break;
+    solve_config(Pa, qs, rel);
+  }
+}
+
+// Many queries in one persistent launch: their configurations form one
+// list of items (query q owns [item0[q], item0[q + 1])), taken in order from
+// one counter.  The host orders the queries by decreasing lattice size, so
+// the longest configurations start first and the short ones fill the tails;
+// a CTA reloads the lattice tables only when its next item belongs to
+// another query.
+__global__ void __launch_bounds__(kMaxThreads, 1) resident_multi_kernel(ResidentBatch B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_item;
+  QueryState qs;
+  int cur = -1;
+  const long long n_items = B.item0[B.nq];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.work, 1ull);
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= n_items) break;
+    int lo = 0, hi = B.nq - 1;  // last q with item0[q] <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (B.item0[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const ResidentArgs& Pa = B.qs[lo];
+    if (lo != cur) {
+      setup_query(Pa, smem_raw, qs);
+      cur = lo;
+    }
+    solve_config(Pa, qs, item - B.item0[lo]);
+  }
+}
+
 // Kernel, dynamic shared memory and grid of a resident launch.
 static pc_status resident_config(const ResidentArgs& args, int threads, void** func, size_t* smem,
                                  long long* grid) {
@@ -477,6 +537,36 @@ pc_status resident_add_node(const ResidentArgs& args, int threads, cudaGraph_t g
   void* params[] = {&a};
   cudaKernelNodeParams kp = {};
   kp.func = func;
+  kp.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = params;
+  PC_CUDA(cudaGraphAddKernelNode(out, g, deps, ndeps, &kp));
+  return PC_OK;
+}
+
+pc_status resident_multi_add_node(const ResidentBatch& b, long long n_items, size_t smem, int threads,
+                                  cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                                  cudaGraphNode_t* out) {
+  if (threads > kMaxThreads || threads < 32 || threads % 32) {
+    set_error("resident solver: CTA size must be a multiple of 32 in [32, 640]");
+    return PC_ERR_ARG;
+  }
+  PC_CUDA(cudaFuncSetAttribute(resident_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0, per_sm = 0;
+  PC_CUDA(cudaGetDevice(&dev));
+  PC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_multi_kernel, threads, smem));
+  if (per_sm < 1) {
+    set_error("resident solver: lattice does not fit one CTA");
+    return PC_ERR_OOM;
+  }
+  long long grid = (long long)per_sm * nsm;
+  if (grid > n_items) grid = n_items;
+  ResidentBatch a = b;
+  void* params[] = {&a};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)resident_multi_kernel;
   kp.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
   kp.blockDim = dim3(threads);
   kp.sharedMemBytes = (unsigned)smem;

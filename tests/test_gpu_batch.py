@@ -129,3 +129,23 @@ def test_batching_workload_full_size_sampled():
                 for key in ("verdict", "first_hit", "m_stop"):
                     assert int(h[key][i]) == int(r[key][0]), (spec, int(i), key)
         assert int(h["n_percolating"][0]) == int(h["verdict"].sum())
+
+
+def test_many_resident_lattices_share_one_launch():
+    """Twelve small lattices of one shared-memory class run in one persistent
+    resident launch: its CTAs move from lattice to lattice (reloading the
+    tables) and every result equals the query's own pc_inspect."""
+    specs = [(W, L, 0.25 + 0.01 * W, 40 + W, 0, 150 + 10 * W)
+             for W, L in [(1, 3), (2, 9), (3, 5), (2, 30), (4, 7), (1, 50), (3, 12),
+                          (5, 4), (2, 2), (4, 20), (6, 3), (3, 1)]]
+    outs, res = pc.pc_batch_run(specs)
+    assert all(r["solver"] == "resident" for r in res)
+    assert len({r["threads"] for r in res}) == 1  # one launch, one CTA size
+    for spec, o in zip(specs, outs):
+        W, L, p, seed, b, n = spec
+        ref = pc.pc_inspect(W, L, p, seed, b, n)
+        _same(o, ref, spec)
+        # the mass differs at most by the order of the final block sum (the
+        # CTA size may differ from the query's own launch)
+        m, r = np.asarray(o["mass"], np.float64), np.asarray(ref["mass"], np.float64)
+        assert np.all(np.abs(m - r) <= 1e-5 * r + 1e-38), spec
