@@ -5,11 +5,13 @@
 //
 // Per slot, G = tube layers whose occupancy is drawn (a multiple of 32, or
 // L) and F = layers prepared (degrees, zeroed nu planes, cleaned reached-set
-// rows).  A tick's units run concurrently, so a plan only uses what earlier
-// ticks completed: step m sweeps layers t <= min(m, L-1) (Eqs. (3)-(4) move
-// mass one layer per step), preparation runs two layers per tick ahead of
-// that window, and the occupancy draw a word row (32 layers) ahead of the
-// preparation.
+// rows; a multiple of 32, or L).  A tick's units run concurrently, so a plan
+// only uses what earlier ticks completed: step m sweeps layers
+// t <= min(m, L-1) (Eqs. (3)-(4) move mass one layer per step); the next word
+// row (32 layers) is prepared once the window comes within 10 layers of the
+// prepared ones, and the occupancy is drawn two word rows ahead of the
+// preparation (the degrees of a row count the occupancy of the row after
+// it).
 #pragma once
 
 #ifdef __CUDACC__
@@ -42,19 +44,19 @@ PC_PLAN_FN Plan make_plan(int phase, int m, int G, int F, int L, int TW) {
     // sentinel column of this one (one unit per column chunk)
     p.hi[U_CLEAN] = 1;
   } else if (phase == PH_PREP0) {
-    p.hi[U_PREP] = L < 5 ? L : 5;
+    p.hi[U_PREP] = L < 32 ? L : 32;  // word row 0
     p.F2 = p.hi[U_PREP];
   } else if (phase == PH_STEP) {
     const int tmax = m < L - 1 ? m : L - 1;
     p.hi[U_FP] = tmax + 1;
     p.hi[U_BITS] = (tmax >> 5) + 1;
-    // two layers prepared per tick (the window grows by one); the degrees of
-    // layer F2 - 1 need the occupancy of layer F2: G >= min(F2 + 1, L)
-    int F2 = F + 2 < L ? F + 2 : L;
-    if (G < (F2 + 1 < L ? F2 + 1 : L)) F2 = F;
+    // the next word row of degrees when the window nears the prepared
+    // layers; the degrees of layer F2 - 1 need the occupancy of layer F2
+    int F2 = F;
+    if (F < L && F < tmax + 10 && G >= (F + 33 < L ? F + 33 : L)) F2 = F + 32 < L ? F + 32 : L;
     p.lo[U_PREP] = F; p.hi[U_PREP] = F2;
     p.F2 = F2;
-    if (G < L && G < F2 + 33) {  // keep occupancy a word row ahead
+    if (G < L && G < F2 + 64) {  // keep occupancy two word rows ahead
       p.lo[U_DRAW] = G >> 5; p.hi[U_DRAW] = (G >> 5) + 1;
       p.G2 = G + 32 < L ? G + 32 : L;
     }

@@ -45,7 +45,8 @@ namespace {
 
 constexpr uint32_t kGrow = 1u, kEnd = 2u;
 constexpr int kCols = 256;    // columns per unit == threads per sweep CTA
-constexpr int kRows = 16;     // layers (or word rows) per BITS / PREP unit
+constexpr int kRows = 16;     // word rows per BITS unit
+constexpr int kBitsCols = 2;  // columns per thread of a BITS unit
 constexpr int kRowsFP = 128;  // layers per FP unit (the ring prologue is paid once per unit)
 constexpr int kMaxRing = 6;  // ring slots: planes in flight ahead of the compute (deeper rings cost L1)
 // shared memory the ring may take per CTA: at least two sweep CTAs fit on an
@@ -61,8 +62,11 @@ inline int ring_depth(int cap) {
   return n < 3 ? 3 : n > kMaxRing ? kMaxRing : n;
 }
 
-// dynamic shared memory of the sweep kernel
-inline int sweep_smem_bytes(int cap, int nring) { return nring * cap * (int)(sizeof(float) + 1); }
+// dynamic shared memory of the sweep kernel: the ring (nring slots of cap
+// FP32 entries, then nring of cap degree bytes) and the tick's unit prefix
+// over the K slots (K + 1 ints)
+__host__ __device__ inline int ring_bytes(int cap, int nring) { return (nring * cap * (int)(sizeof(float) + 1) + 15) & ~15; }
+inline int sweep_smem_bytes(int cap, int nring, int K) { return ring_bytes(cap, nring) + 4 * (K + 1); }
 
 struct QDev {
   Lattice lat;
@@ -106,6 +110,7 @@ struct Ctx {
   cudaGraphConditionalHandle cond;
   int seg_cap;                  // floats per shared-memory ring slot of the FP units
   int nring;                    // ring slots (3 .. kMaxRing)
+  int fp;                       // some query runs the FP32 recursion (else: the bits-only kernel)
   int use_cond;                 // set the WHILE condition at the end of a tick
   int server;                   // 1: slots are bound to a query by the host
   char** slot_base;             // [K] state of each slot (server mode)
@@ -124,10 +129,13 @@ __host__ __device__ inline int width_of(int kind, const Lattice& lat) {
   return (kind == U_PREP || kind == U_CLEAN) ? lat.P : lat.A;
 }
 
+// items of one unit row per kind (a BITS unit thread takes kBitsCols columns)
+__host__ __device__ inline int unit_width(int kind) { return kind == U_BITS ? kCols * kBitsCols : kCols; }
+
 __host__ __device__ inline int units_of(int kind, int lo, int hi, const Lattice& lat) {
   if (hi <= lo) return 0;
-  const int ccol = (width_of(kind, lat) + kCols - 1) / kCols;
-  const int per = (kind == U_DRAW || kind == U_CLEAN) ? 1 : kind == U_FP ? kRowsFP : kRows;
+  const int ccol = (width_of(kind, lat) + unit_width(kind) - 1) / unit_width(kind);
+  const int per = (kind == U_DRAW || kind == U_CLEAN) ? 1 : kind == U_FP ? kRowsFP : kind == U_PREP ? 32 : kRows;
   return ccol * ((hi - lo + per - 1) / per);
 }
 
@@ -440,10 +448,16 @@ __device__ __forceinline__ void fp_unit_staged(const Ctx& x, const Lattice& lat,
   }
 }
 
-__global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
-  // x.nring slots of x.seg_cap floats (nu planes), then x.nring of x.seg_cap bytes (degrees)
+// kFP = false: a plan without FP32 work (every query PC_BITS_ONLY) -- no
+// ring, no FP units, fewer registers and more CTAs per SM for the
+// latency-bound bit units.
+template <bool kFP>
+__global__ void __launch_bounds__(kCols, kFP ? 2 : 4) sweep_kernel(Ctx x) {
+  // x.nring slots of x.seg_cap floats (nu planes), then x.nring of x.seg_cap
+  // bytes (degrees), then the tick's unit prefix over the slots
   extern __shared__ __align__(128) float ring[];
   uint8_t* dring = reinterpret_cast<uint8_t*>(ring + (size_t)x.nring * x.seg_cap);
+  int* s_pre = reinterpret_cast<int*>(reinterpret_cast<char*>(ring) + ring_bytes(x.seg_cap, x.nring));
   __shared__ float inv_deg[16];
   __shared__ uint32_t s_flag;
   __shared__ int s_red[2];
@@ -456,11 +470,14 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
     for (int i = 0; i < x.nring; ++i) mbar_init(&bars[i], 1);  // one arrival plus the bytes
     mbar_fence_init();
   }
+  // the tick's unit prefix, searched for every unit: staged once per CTA
+  for (int s = tid; s <= x.K; s += blockDim.x) s_pre[s] = x.pre[s];
   __syncthreads();
   Ring rg{0, 0u, 0, 0, 0, false};
-  const int total = x.pre[x.K];
+  const int total = s_pre[x.K];
   // units are taken from a tick-wide counter (double-buffered broadcast: one
-  // block barrier per unit)
+  // block barrier per unit).  A CTA asks for its next unit only when it is
+  // free: reserving one ahead holds back long units at the end of a tick.
   __shared__ int s_unit[2];
   for (int it = 0;; ++it) {
     if (tid == 0) s_unit[it & 1] = (int)atomicAdd(x.next_unit, 1u);
@@ -471,22 +488,34 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
     int lo = 0, hi = x.K - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (x.pre[mid] <= u) lo = mid; else hi = mid - 1;
+      if (s_pre[mid] <= u) lo = mid; else hi = mid - 1;
     }
     const int slot = lo;
     const Ctl c = x.ctl[slot];
-    int local = u - x.pre[slot], kind = 0;
-    while (local >= c.units[kind]) { local -= c.units[kind]; ++kind; }
+    // a slot's units in the order preparation, draw, FP, bits, clean: the
+    // occasional long preparation and draw units start early in the tick
+    // instead of lengthening its end
+    constexpr int kOrder[U_KINDS] = {U_PREP, U_DRAW, U_FP, U_BITS, U_CLEAN};
+    // (unrolled: constant indices keep the slot's control block in registers)
+    int local = u - s_pre[slot], kind = -1;
+#pragma unroll
+    for (int i = 0; i < U_KINDS; ++i) {
+      const int n = c.units[kOrder[i]];
+      if (kind < 0) {
+        if (local < n) kind = kOrder[i];
+        else local -= n;
+      }
+    }
     const QDev& Q = x.qs[c.q];
     const Lattice& lat = Q.lat;
     const int A = lat.A, L = lat.L, S = lat.S, P = lat.P;
-    const int ccol = (width_of(kind, lat) + kCols - 1) / kCols;
+    const int ccol = (width_of(kind, lat) + unit_width(kind) - 1) / unit_width(kind);
     const int cchunk = local % ccol, rchunk = local / ccol;
-    const int a = cchunk * kCols + tid;  // column, strip or plane position
+    const int a = cchunk * unit_width(kind) + tid;  // column, strip pair or plane position
     const Plan p = make_plan(c.phase, c.m, c.G, c.F, L, lat.TW);
     const SlotView v = view_of(x, slot, lat);
 
-    if (kind == U_FP) {
+    if (kFP && kind == U_FP) {
       const int t0 = p.lo[U_FP] + rchunk * kRowsFP;
       const int t1 = min(t0 + kRowsFP, p.hi[U_FP]);
       fp_unit_staged(x, lat, v, (c.m & 1) != 0, cchunk * kCols, t0, t1, ring, dring, bars, rg, &s_abort,
@@ -501,6 +530,8 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
         return;
       }
     } else if (kind == U_BITS) {
+      // columns a and a + kCols (kBitsCols per thread) and two word rows
+      // per iteration: four independent load chains in flight per thread
       const int w0 = p.lo[U_BITS] + rchunk * kRows;
       const int w1 = min(w0 + kRows, p.hi[U_BITS]);
       const bool odd = (c.m & 1) != 0;
@@ -509,38 +540,52 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
       const uint32_t* __restrict__ Rs = odd ? v.R0 : v.R1;
       uint32_t* __restrict__ Rd = odd ? v.R1 : v.R0;
       const uint32_t* __restrict__ occw = v.occw;
+      const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
       uint32_t fl = 0;
-      if (a < A) {
-        const int sg = lat.sigma[a];
-        int nb[kLateral];
+      int col[kBitsCols], nb[kBitsCols][kLateral];
+      uint32_t sh_up[kBitsCols], sh_dn[kBitsCols];
 #pragma unroll
-        for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[a * kLateral + d];
-        const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
+      for (int k = 0; k < kBitsCols; ++k) {
+        // a thread past the last column takes the sentinel column A: its
+        // words are zero and its contacts the sentinel again, so it reads in
+        // bounds and writes nothing
+        col[k] = a + k * kCols < A ? a + k * kCols : A;
+        const int cc = col[k] < A ? col[k] : 0;
+        const int sg = lat.sigma[cc];
+#pragma unroll
+        for (int d = 0; d < kLateral; ++d) nb[k][d] = col[k] < A ? lat.nbr[cc * kLateral + d] : A;
         // the up contacts reach tube t+1 from sigma = 2, the down contacts
         // tube t-1 from sigma = 0: one funnel shift of their ORed words
-        const uint32_t sh_up = sg == 2 ? 1u : 0u, sh_dn = sg == 0 ? 1u : 0u;
+        sh_up[k] = sg == 2 ? 1u : 0u;
+        sh_dn[k] = sg == 0 ? 1u : 0u;
+      }
 #pragma unroll 2
-        for (int tw = w0; tw < w1; ++tw) {
-          const uint32_t* r0 = Rs + (size_t)tw * S;  // word tw - 1
-          const uint32_t* r1 = r0 + S;               // word tw
-          const uint32_t* r2 = r1 + S;               // word tw + 1
-          const uint32_t old = __ldg(r1 + a);
+      for (int tw = w0; tw < w1; ++tw) {
+        const uint32_t* r0 = Rs + (size_t)tw * S;  // word tw - 1
+        const uint32_t* r1 = r0 + S;               // word tw
+        const uint32_t* r2 = r1 + S;               // word tw + 1
+#pragma unroll
+        for (int k = 0; k < kBitsCols; ++k) {
+          const int ak = col[k];
+          const uint32_t old = __ldg(r1 + ak);
           // end contacts: tubes t-1 and t+1 of the own column
-          uint32_t acc = ((old << 1) | (__ldg(r0 + a) >> 31)) | ((old >> 1) | (__ldg(r2 + a) << 31));
+          uint32_t acc = ((old << 1) | (__ldg(r0 + ak) >> 31)) | ((old >> 1) | (__ldg(r2 + ak) << 31));
           // same-layer contacts (d = 0..5): same tube index
 #pragma unroll
-          for (int d = 0; d < 6; ++d) acc |= __ldg(r1 + nb[d]);
-          const uint32_t up = __ldg(r1 + nb[6]) | __ldg(r1 + nb[7]) | __ldg(r1 + nb[8]);
-          const uint32_t up_hi = __ldg(r2 + nb[6]) | __ldg(r2 + nb[7]) | __ldg(r2 + nb[8]);
-          const uint32_t dn = __ldg(r1 + nb[9]) | __ldg(r1 + nb[10]) | __ldg(r1 + nb[11]);
-          const uint32_t dn_lo = __ldg(r0 + nb[9]) | __ldg(r0 + nb[10]) | __ldg(r0 + nb[11]);
+          for (int d = 0; d < 6; ++d) acc |= __ldg(r1 + nb[k][d]);
+          const uint32_t up = __ldg(r1 + nb[k][6]) | __ldg(r1 + nb[k][7]) | __ldg(r1 + nb[k][8]);
+          const uint32_t up_hi = __ldg(r2 + nb[k][6]) | __ldg(r2 + nb[k][7]) | __ldg(r2 + nb[k][8]);
+          const uint32_t dn = __ldg(r1 + nb[k][9]) | __ldg(r1 + nb[k][10]) | __ldg(r1 + nb[k][11]);
+          const uint32_t dn_lo = __ldg(r0 + nb[k][9]) | __ldg(r0 + nb[k][10]) | __ldg(r0 + nb[k][11]);
           // bit b of the result = contact at tube 32 tw + b (+1 for up, -1 for down)
-          acc |= __funnelshift_r(up, up_hi, sh_up) | __funnelshift_l(dn_lo, dn, sh_dn);
-          const int wi = (tw + 1) * S + a;
+          acc |= __funnelshift_r(up, up_hi, sh_up[k]) | __funnelshift_l(dn_lo, dn, sh_dn[k]);
+          const int wi = (tw + 1) * S + ak;
           const uint32_t nw = old | (acc & __ldg(occw + wi));
-          Rd[wi] = nw;
-          if (nw != old) fl |= kGrow;
-          if (tw == endw && (((nw & ~old) >> endb) & 1u)) fl |= kEnd;
+          if (ak < A) {
+            Rd[wi] = nw;
+            if (nw != old) fl |= kGrow;
+            if (tw == endw && (((nw & ~old) >> endb) & 1u)) fl |= kEnd;
+          }
         }
       }
       fl = __reduce_or_sync(0xffffffffu, fl);
@@ -550,35 +595,57 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
       __syncthreads();
       if (tid == 0 && s_flag) atomicOr(&x.ctl[slot].flags, s_flag);
     } else if (kind == U_PREP) {
-      const int t0 = p.lo[U_PREP] + rchunk * kRows;
-      const int t1 = min(t0 + kRows, p.hi[U_PREP]);
+      // one word row (32 layers, t0 a multiple of 32) of plane position a:
+      // degrees counted for 32 tubes at once -- each contact's occupancy
+      // word, shifted to the row by the contact's tube offset, added into a
+      // 4-bit counter held as four bit planes (at most 14 contacts) -- then
+      // written one byte per layer, the nu planes zeroed, and the
+      // reached-set word row after this one cleaned
+      const int t0 = p.lo[U_PREP] + rchunk * 32;
+      const int t1 = min(t0 + 32, p.hi[U_PREP]);
       const int pos = a;
       if (pos < P) {
         const int col = __ldg(lat.pcol + pos);
-        int nb[kLateral];
-        int sg = 0;
-        if (col >= 0) {
-          sg = lat.sigma[col];
+        const int w = t0 >> 5;
+        uint32_t cnt0 = 0u, cnt1 = 0u, cnt2 = 0u, cnt3 = 0u, own = 0u;
+        if (col >= 0 && !Q.bits_only) {
+          const int sg = lat.sigma[col];
+          const uint32_t* o0 = v.occw + (size_t)w * S;  // word w - 1
+          const uint32_t* o1 = o0 + S;                  // word w
+          const uint32_t* o2 = o1 + S;                  // word w + 1
+          auto add = [&](uint32_t x) {  // bit-sliced counter += x
+            uint32_t c = cnt0 & x; cnt0 ^= x;
+            uint32_t c2 = cnt1 & c; cnt1 ^= c;
+            c = cnt2 & c2; cnt2 ^= c2;
+            cnt3 ^= c;
+          };
+          own = o1[col];
+          add((own << 1) | (o0[col] >> 31));  // tube t-1
+          add((own >> 1) | (o2[col] << 31));  // tube t+1
+          const uint32_t sh_up = sg == 2 ? 1u : 0u, sh_dn = sg == 0 ? 1u : 0u;
 #pragma unroll
-          for (int d = 0; d < kLateral; ++d) nb[d] = lat.nbr[col * kLateral + d];
+          for (int d = 0; d < kLateral; ++d) {
+            const int nb = lat.nbr[col * kLateral + d];
+            if (d < 6) add(o1[nb]);
+            else if (d < 9) add(__funnelshift_r(o1[nb], o2[nb], sh_up));
+            else add(__funnelshift_l(o0[nb], o1[nb], sh_dn));
+          }
         }
         for (int t = t0; t < t1; ++t) {
+          const int b = t - t0;
           int deg = 0;
-          if (col >= 0 && !Q.bits_only && bit_at(v.occw, S, col, t)) {
-            deg = (int)bit_at(v.occw, S, col, t - 1) + (int)bit_at(v.occw, S, col, t + 1) + (t == L - 1);
-#pragma unroll
-            for (int d = 0; d < kLateral; ++d) deg += (int)bit_at(v.occw, S, nb[d], t + dir_dt(d, sg));
-          }
+          if ((own >> b) & 1u)
+            deg = (int)(((cnt0 >> b) & 1u) | (((cnt1 >> b) & 1u) << 1) | (((cnt2 >> b) & 1u) << 2) |
+                        (((cnt3 >> b) & 1u) << 3)) + (t == L - 1);
           if (!Q.bits_only) {
             v.dg[(size_t)t * P + pos] = (uint8_t)deg;
             v.nu0[(size_t)(t + 2) * P + pos] = 0.f;
             v.nu1[(size_t)(t + 2) * P + pos] = 0.f;
           }
-          if (col >= 0 && (t & 31) == 0) {  // reached-set word rows cleaned one row ahead
-            const int wr = (t >> 5) + 2;
-            v.R0[wr * S + col] = 0u; v.R1[wr * S + col] = 0u;
-            if (t == 0) { v.R0[S + col] = 0u; v.R1[S + col] = 0u; }
-          }
+        }
+        if (col >= 0) {  // reached-set word rows cleaned one row ahead
+          v.R0[(w + 2) * S + col] = 0u; v.R1[(w + 2) * S + col] = 0u;
+          if (w == 0) { v.R0[S + col] = 0u; v.R1[S + col] = 0u; }
         }
       }
     } else if (kind == U_CLEAN) {
@@ -627,14 +694,19 @@ __global__ void __launch_bounds__(kCols, 2) sweep_kernel(Ctx x) {
   }
 }
 
+// The sweep kernel a plan launches.
+inline const void* sweep_fn(const Ctx& x) {
+  return x.fp ? (const void*)sweep_kernel<true> : (const void*)sweep_kernel<false>;
+}
+
 // Persistent sweep grid: as many CTAs as fit on the device at once (units
 // are fetched dynamically, so more CTAs would only add start-up work).
 int sweep_grid(const Ctx& x) {
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, kCols,
-                                                    sweep_smem_bytes(x.seg_cap, x.nring)) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_fn(x), kCols,
+                                                    sweep_smem_bytes(x.seg_cap, x.nring, x.K)) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
@@ -843,13 +915,15 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   x.pool = q;
   x.slot_bytes = slot;
   x.use_cond = 0; x.server = 0; x.slot_base = nullptr; x.qnext = nullptr; x.qdone = nullptr;
+  x.fp = 0;
+  for (int i = 0; i < nq; ++i) x.fp |= qs[i].bits_only ? 0 : 1;
   {
     int cap = 16;
     for (int i = 0; i < nq; ++i) cap = std::max(cap, max_pair_segment(qs[i].lat.W, kCols) + 16);
-    x.seg_cap = cap;
-    x.nring = ring_depth(cap);
-    const int bytes = sweep_smem_bytes(cap, x.nring);
-    cudaError_t ea = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    x.seg_cap = x.fp ? cap : 0;
+    x.nring = x.fp ? ring_depth(cap) : 0;
+    const int bytes = sweep_smem_bytes(x.seg_cap, x.nring, x.K);
+    cudaError_t ea = cudaFuncSetAttribute(sweep_fn(x), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (ea != cudaSuccess) { cudaFreeAsync(P->mem, st); delete P; return cuda_fail(ea, "sweep smem"); }
   }
   // every configuration needs at most N + 3 ticks; slots run concurrently
@@ -894,9 +968,9 @@ pc_status stream_plan_add(StreamPlan* P, cudaGraph_t g, const cudaGraphNode_t* d
   PC_CUDA(cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaKernelNodeParams sp = {};
-  sp.func = (void*)sweep_kernel;
+  sp.func = const_cast<void*>(sweep_fn(x));
   sp.gridDim = dim3(P->grid); sp.blockDim = dim3(kCols); sp.kernelParams = args;
-  sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring);
+  sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring, x.K);
   cudaGraphNode_t n_sweep, n_ctl;
   PC_CUDA(cudaGraphAddKernelNode(&n_sweep, body, nullptr, 0, &sp));
   cudaKernelNodeParams cpk = {};
@@ -1004,7 +1078,7 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
   x.error = (int*)(x.ticks + 2);
   x.next_unit = x.ticks + 3;
   x.pool = nullptr; x.slot_bytes = 0; x.max_ticks = 0xffffffffu;
-  x.use_cond = 0; x.server = 1;
+  x.use_cond = 0; x.server = 1; x.fp = 1;  // served queries may run the FP32 recursion
   x.seg_cap = max_pair_segment(max_W, kCols) + 16;  // any lattice the server accepts
   x.nring = ring_depth(x.seg_cap);
   E->max_queries = nq;
@@ -1021,8 +1095,8 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  sweep_smem_bytes(x.seg_cap, x.nring))) != cudaSuccess) {
+    if ((e = cudaFuncSetAttribute(sweep_fn(x), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sweep_smem_bytes(x.seg_cap, x.nring, x.K))) != cudaSuccess) {
       rc = cuda_fail(e, "sweep smem"); break;
     }
     cudaGraph_t g;
@@ -1031,9 +1105,9 @@ pc_status server_engine_create(int max_slots, int max_queries, int ticks_per_chu
     cudaGraphNode_t prev = nullptr;
     for (int t = 0; t < std::max(1, ticks_per_chunk) && rc == PC_OK; ++t) {
       cudaKernelNodeParams sp = {};
-      sp.func = (void*)sweep_kernel; sp.gridDim = dim3(sweep_grid(x)); sp.blockDim = dim3(kCols);
+      sp.func = const_cast<void*>(sweep_fn(x)); sp.gridDim = dim3(sweep_grid(x)); sp.blockDim = dim3(kCols);
       sp.kernelParams = args;
-      sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring);
+      sp.sharedMemBytes = (unsigned)sweep_smem_bytes(x.seg_cap, x.nring, x.K);
       cudaGraphNode_t ns, nc;
       if ((e = cudaGraphAddKernelNode(&ns, g, prev ? &prev : nullptr, prev ? 1 : 0, &sp)) != cudaSuccess) { rc = cuda_fail(e, "node"); break; }
       cudaKernelNodeParams cp = {};
@@ -1130,7 +1204,8 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st) {
     unsigned long long done = 0;
     for (int chunk = 0; rc == PC_OK && done < (unsigned long long)x.n_items; ++chunk) {
       for (int i = 0; i < 32; ++i) {
-        sweep_kernel<<<P->grid, kCols, sweep_smem_bytes(x.seg_cap, x.nring), st>>>(x);
+        if (x.fp) sweep_kernel<true><<<P->grid, kCols, sweep_smem_bytes(x.seg_cap, x.nring, x.K), st>>>(x);
+        else sweep_kernel<false><<<P->grid, kCols, sweep_smem_bytes(x.seg_cap, x.nring, x.K), st>>>(x);
         control_kernel<<<x.K, kCols, 0, st>>>(x);
       }
       int err = 0;

@@ -7,7 +7,8 @@
 //   * the BITS units update word rows <= tmax/32 from their occupancy:
 //     G >= min(32 (tmax/32 + 1), L) layers are drawn;
 //   * the preparation of layers [F, F2) needs the occupancy of layer F2
-//     (degrees of layer F2 - 1): G >= min(F2 + 1, L);
+//     (degrees of layer F2 - 1): G >= min(F2 + 1, L); it covers whole word
+//     rows: F and F2 multiples of 32, or L;
 //   * one draw unit per tick, on the next word row, G a multiple of 32 or L;
 //   * F and G never shrink and reach L.
 #include <cstdio>
@@ -29,7 +30,7 @@ static int check(int L) {
   int G = p.G2, F = 0;
   if (G != (64 < L ? 64 : L)) return fail(L, 0, "first draw size");
   p = make_plan(PH_PREP0, 0, G, F, L, TW);
-  if (p.lo[U_PREP] != 0 || p.hi[U_PREP] != (L < 5 ? L : 5)) return fail(L, 0, "first preparation");
+  if (p.lo[U_PREP] != 0 || p.hi[U_PREP] != (L < 32 ? L : 32)) return fail(L, 0, "first preparation");
   if (G < (p.hi[U_PREP] + 1 < L ? p.hi[U_PREP] + 1 : L)) return fail(L, 0, "first preparation before draw");
   F = p.F2;
   if (L == 1) return 0;
@@ -45,6 +46,7 @@ static int check(int L) {
       return fail(L, m, "preparation range");
     if (p.hi[U_PREP] > F && G < (p.hi[U_PREP] + 1 < L ? p.hi[U_PREP] + 1 : L))
       return fail(L, m, "degrees before the occupancy they count");
+    if (p.hi[U_PREP] != L && p.hi[U_PREP] % 32 != 0) return fail(L, m, "preparation not on a word row");
     if (p.hi[U_DRAW] > p.lo[U_DRAW]) {
       if (p.hi[U_DRAW] != p.lo[U_DRAW] + 1 || p.lo[U_DRAW] != (G >> 5) || p.lo[U_DRAW] >= TW)
         return fail(L, m, "draw row");
