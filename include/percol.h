@@ -344,6 +344,23 @@ pc_status pc_stream_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_s
                            int16_t* strip_row, int32_t* row_off, int32_t* ppos, int32_t* pcol);
 
 /*
+ * Shape of the verdict-only solver with temporal blocking on the current
+ * device (diagnostics and tests).  PC_BITS_ONLY inspections on the streamed
+ * path run 32 steps per visit of a slab of word rows when one thread-block
+ * cluster can hold every column of the lattice's cross-section in shared
+ * memory (Sec. II.B: the reached set alone decides the verdict, first_hit
+ * and m_stop).  Outputs (each may be NULL): cluster_size (CTAs per cluster,
+ * 1..16), columns_per_cta (cross-section columns each CTA owns, one per
+ * thread), slab_rows (32-tube word rows per slab in shared memory, the valid
+ * rows plus one halo row above and one below), clusters (clusters the device
+ * runs at once).  Errors: PC_ERR_ARG (W outside [0, 255], or no cluster of
+ * this device holds the cross-section -- the step-synchronous solver then
+ * runs such inspections), PC_ERR_CUDA (no device).
+ */
+pc_status pc_bits_blocked_shape(int32_t W, int32_t* cluster_size, int32_t* columns_per_cta,
+                                int32_t* slab_rows, int32_t* clusters);
+
+/*
  * The lazy walk of the self-loop remark in Sec. II.B: at every step the
  * electron stays on its site with probability hold, otherwise it moves as
  * Eq. (2) says (the chain hold * I + (1 - hold) * P).  Percolation, first_hit

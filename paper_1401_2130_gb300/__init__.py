@@ -54,6 +54,7 @@ SIGNATURES = {
     "pc_server_destroy": [_vp],
     "pc_lattice_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "pc_stream_layout": [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "pc_bits_blocked_shape": [_i32, _vp, _vp, _vp, _vp],
     "pc_lazy_mass": [_vp, _vp, _i64, _dbl, _vp, _i32, _vp],
     "pc_shutdown": [],
     "pc_last_error": [],
@@ -134,6 +135,19 @@ def pc_lattice_layout(W: int) -> dict:
     _check(lib.pc_lattice_layout(W, None, None, None, _ptr(sr), _ptr(ro), _ptr(pp), _ptr(pcl)))
     return {"P": P.value, "s_begin": sb.value, "n_strips": ns.value, "strip_row": sr,
             "row_off": ro, "ppos": pp, "pcol": pcl}
+
+
+def pc_bits_blocked_shape(W: int) -> dict | None:
+    """Cluster shape of the verdict-only solver with temporal blocking for
+    radius W on the current device, or None where the step-synchronous
+    solver runs PC_BITS_ONLY inspections instead (see percol.h)."""
+    lib = load()
+    v = [ctypes.c_int32() for _ in range(4)]
+    st = lib.pc_bits_blocked_shape(W, *[ctypes.addressof(x) for x in v])
+    if st == PC_ERR_ARG and 0 <= W <= 255:
+        return None
+    _check(st)
+    return dict(zip(("cluster_size", "columns_per_cta", "slab_rows", "clusters"), (x.value for x in v)))
 
 
 def pc_stream_layout(W: int) -> dict:

@@ -1,0 +1,546 @@
+// blocked.cu -- the verdict-only (PC_BITS_ONLY) streamed solver with temporal
+// blocking: 32 steps of the exact reached-set propagation per visit of a
+// slab, the whole hexagonal cross-section held on chip by one thread-block
+// cluster (Sec. II.B: only whether mass can reach a site matters, so the
+// reached set R_m -- sites with nonzero mass at some step <= m -- decides
+// the verdict; the first step that reaches the detector layer L-1 gives
+// first_hit, the first step without growth m_stop).
+//
+// Why a cluster.  One step moves the reached set by at most one tube along
+// the fibre, but across the cross-section the same-layer contacts jump two
+// hexagon rows.  A tile of the cross-section would need a lateral halo of
+// two rows per step, which at W = 64 (a hexagon 129 rows wide) leaves no
+// useful interior after a few steps.  A cluster of up to 16 CTAs instead
+// holds every column of the lattice (CTA r owns columns [r cpr, (r+1) cpr),
+// one per thread), so the only halo is along t: one 32-tube word row above
+// and below the slab, which 32 steps cannot cross.
+//
+// Slab ("tile") of a pass: valid word rows [w0, w0 + nw) plus the halo rows
+// w0 - 1 and w0 + nw, in shared memory as rows x (cpr + 1) words (column
+// cpr is the always-zero stand-in for contacts outside the hexagon), with
+// the occupancy words beside them.  Each step reads a column's own words,
+// its six same-layer contacts and the three up / three down contacts of the
+// neighbouring rows from the owning CTA's shared memory (ld.shared::cluster),
+// writes the new words to the other buffer, and ends with a cluster barrier.
+// A step's growth and detector hit are ORed, per step, into a 32-bit mask of
+// the configuration; valid rows of different slabs partition the layers, so
+// the masks are exact.  After the pass the control kernel takes the first
+// step that hit the detector or did not grow; the state after a terminating
+// step is never used.
+//
+// Per configuration ("slot") in HBM: occupancy and two reached-set buffers,
+// word [w][a] = tubes 32w .. 32w+31 of column a.  Rows are never cleaned: a
+// pass starting after step m0 reads row w only if 32 w <= m0 (higher rows
+// are empty at that step, whatever a previous configuration left there), and
+// occupancy only up to the rows 32 steps can reach.  Occupancy is drawn
+// lazily, one word row per pass, with the same Philox stream as every other
+// path (counter (t A + a) >> 2, lane (t A + a) & 3).
+//
+// One tick = one pass kernel (persistent clusters taking slabs and draw
+// rows from a counter) and one control kernel (one CTA per slot: masks ->
+// outputs, refill, plan of the next pass).  The host launches ticks in
+// chunks and reads the completion count between chunks.
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kSteps = 32;       // steps per pass (one word row of halo on each side)
+constexpr int kMaxThreads = 1024;
+constexpr int kMaxRows = 34;     // slab rows in shared memory (valid rows + 2 halo rows)
+constexpr int kCtlThreads = 256;
+constexpr int kChunk = 16;       // ticks launched between reads of the completion count
+
+enum : int { BP_EMPTY = 0, BP_DRAW0 = 1, BP_STEP = 2 };
+
+inline size_t a256_host(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct BSlot {
+  long long item;    // configuration (index within the query)
+  int phase;
+  int m0;            // steps done
+  int G;             // word rows of occupancy drawn
+  int par;           // reached-set buffer holding step m0
+  int tiles, draws;  // slabs and drawn rows of the pass in flight
+  unsigned gmask;    // bit j: step m0 + 1 + j grew the reached set
+  unsigned hmask;    // bit j: step m0 + 1 + j reached layer L - 1
+};
+
+struct BCtx {
+  Lattice lat;
+  OccStream occ;
+  const uint32_t* occ_bits;
+  int64_t words_per_cfg;
+  int64_t n_cfg;
+  uint32_t cfg0;
+  Outputs out;
+  int K;
+  BSlot* slot;
+  int* pre;                    // [K + 1] prefix of pass items over slots
+  uint32_t* pool;              // per slot: occupancy, R0, R1 (TW x A words each)
+  size_t slot_words;
+  unsigned long long* work;    // next configuration
+  unsigned long long* n_done;
+  unsigned* next_item;
+  unsigned* arrive;
+  unsigned* ticks;
+  int* error;
+  int cpr;                     // columns per CTA of a cluster
+  int nrow;                    // slab rows in shared memory
+  int nw;                      // valid rows per slab (nrow - 2)
+};
+
+// --- cluster primitives (PTX ISA: mapa, ld.shared::cluster, barrier.cluster)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders shared-memory accesses
+// before it against those after it, cluster-wide
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t map_rank(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint32_t ldc(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+// Occupancy word (tubes 32 tw .. 32 tw + 31) of column a: the same stream as
+// every other path draws.
+__device__ inline uint32_t draw_word(const BCtx& x, long long rel, int tw, int a) {
+  const int A = x.lat.A, L = x.lat.L;
+  uint32_t word = 0;
+  if (x.occ_bits) {
+    const uint32_t* cb = x.occ_bits + (size_t)rel * x.words_per_cfg;
+    for (int b = 0; b < 32; ++b) {
+      const int t = tw * 32 + b;
+      if (t >= L) break;
+      const int64_t i = (int64_t)t * A + a;
+      word |= ((cb[i >> 5] >> (i & 31)) & 1u) << b;
+    }
+  } else {
+    const uint32_t cfg = x.cfg0 + (uint32_t)rel;
+    for (int b = 0; b < 32; ++b) {
+      const int t = tw * 32 + b;
+      if (t >= L) break;
+      const int64_t i = (int64_t)t * A + a;
+      const u32x4 r = philox4x32_10(u32x4{(uint32_t)(i >> 2), cfg, x.occ.wl, 0u}, x.occ.k0, x.occ.k1);
+      const uint32_t w = (i & 3) == 0 ? r.x : (i & 3) == 1 ? r.y : (i & 3) == 2 ? r.z : r.w;
+      word |= (uint32_t)((uint64_t)w < x.occ.T) << b;
+    }
+  }
+  return word;
+}
+
+// Items of a slot's next pass (slabs, then rows to draw).
+__device__ inline void plan_slot(const BCtx& x, BSlot& c) {
+  const int TW = x.lat.TW;
+  c.tiles = 0; c.draws = 0;
+  if (c.phase == BP_DRAW0) {
+    c.draws = TW < 2 ? TW : 2;  // rows 0 and 1: what the first pass reads
+  } else if (c.phase == BP_STEP) {
+    const int rtop = min((c.m0 + kSteps) >> 5, TW - 1);  // highest row 32 more steps can reach
+    c.tiles = (rtop + 1 + x.nw - 1) / x.nw;
+    // the next pass reads one row more: draw it now
+    if (c.G < TW && c.G <= ((c.m0 + 2 * kSteps) >> 5)) c.draws = 1;
+  }
+}
+
+__device__ inline void take(const BCtx& x, BSlot& c, unsigned long long item) {
+  c.item = (long long)item; c.m0 = 0; c.G = 0; c.par = 0; c.gmask = 0u; c.hmask = 0u;
+  c.phase = (long long)item < x.n_cfg ? BP_DRAW0 : BP_EMPTY;
+  plan_slot(x, c);
+}
+
+__device__ void prefix_items(const BCtx& x) {
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int s = 0; s < x.K; ++s) {
+      x.pre[s] = acc;
+      acc += x.slot[s].tiles + x.slot[s].draws;
+    }
+    x.pre[x.K] = acc;
+  }
+}
+
+__global__ void blocked_init_kernel(BCtx x) {
+  for (int s = threadIdx.x; s < x.K; s += blockDim.x) {
+    BSlot c;
+    take(x, c, (unsigned long long)s);
+    x.slot[s] = c;
+  }
+  __syncthreads();
+  prefix_items(x);
+  if (threadIdx.x == 0) {
+    *x.work = (unsigned long long)x.K;
+    *x.n_done = 0ull; *x.next_item = 0u; *x.arrive = 0u; *x.ticks = 0u;
+  }
+}
+
+// One pass: every slab of every active slot (32 steps each) and the rows to
+// draw.  Grid = whole clusters, persistent; items are taken cluster-wide.
+__global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int s_item[2];
+  __shared__ unsigned s_g, s_h;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t rank = cluster_rank();
+  const int A = x.lat.A, L = x.lat.L, TW = x.lat.TW;
+  const int stride = x.cpr + 1;       // words per slab row
+  const int plane = x.nrow * stride;  // words per array
+  uint32_t* B0 = sm;
+  uint32_t* B1 = sm + plane;
+  uint32_t* O = sm + 2 * plane;
+  const int c0 = (int)rank * x.cpr;
+  const int ncol = max(0, min(x.cpr, A - c0));
+  for (int i = tid; i < 3 * x.nrow; i += nt) sm[i * stride + x.cpr] = 0u;  // zero column
+  if (tid == 0) { s_g = 0u; s_h = 0u; }
+  // cluster addresses of this column's contacts in row 0 of B0 (a contact
+  // outside the hexagon reads the zero column)
+  const bool own = tid < ncol;
+  const int col = c0 + tid;
+  uint32_t nb[kLateral];
+  int sg = 0;
+  if (own) {
+    sg = x.lat.sigma[col];
+#pragma unroll
+    for (int d = 0; d < kLateral; ++d) {
+      const int j = x.lat.nbr[col * kLateral + d];
+      const int r = j >= A ? (int)rank : j / x.cpr;
+      const int l = j >= A ? x.cpr : j - r * x.cpr;
+      nb[d] = map_rank(B0 + l, (uint32_t)r);
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < kLateral; ++d) nb[d] = 0u;
+  }
+  // the up contacts reach tube t+1 from sigma = 2, the down contacts tube t-1
+  // from sigma = 0: one funnel shift of their ORed words
+  const uint32_t sh_up = sg == 2 ? 1u : 0u, sh_dn = sg == 0 ? 1u : 0u;
+  const uint32_t planeb = (uint32_t)plane * 4u, rowb = (uint32_t)stride * 4u;
+  const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
+  const uint32_t item_addr = map_rank(&s_item[0], 0u);
+  cluster_sync_all();
+
+  for (int it = 0;; ++it) {
+    if (rank == 0 && tid == 0) s_item[it & 1] = (int)atomicAdd(x.next_item, 1u);
+    cluster_sync_all();
+    const int item = (int)ldc(item_addr + 4u * (uint32_t)(it & 1));
+    if (item >= x.pre[x.K]) break;  // the same value in every CTA of the cluster
+    int lo = 0, hi = x.K - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (x.pre[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int s = lo;
+    const BSlot c = x.slot[s];
+    const int local = item - x.pre[s];
+    uint32_t* occw = x.pool + (size_t)s * x.slot_words;
+    uint32_t* R0 = occw + (size_t)TW * A;
+    uint32_t* R1 = R0 + (size_t)TW * A;
+
+    if (local >= c.tiles) {  // one row of occupancy for the next pass
+      const int tw = c.G + (local - c.tiles);
+      if (own) occw[(size_t)tw * A + col] = draw_word(x, c.item, tw, col);
+      continue;
+    }
+
+    // slab: local row i holds word row w0 - 1 + i
+    const int w0 = local * x.nw;
+    const int m0 = c.m0;
+    const int rtop = min((m0 + kSteps) >> 5, TW - 1);
+    const int n_eff = min(x.nrow, rtop - w0 + 2);  // rows above rtop stay empty for 32 steps
+    const int ivmax = min(x.nw, n_eff - 1);        // valid rows 1 .. ivmax
+    const int iend = endw - (w0 - 1);
+    const uint32_t* Rs = c.par ? R1 : R0;
+    uint32_t* Rd = c.par ? R0 : R1;
+    if (own) {
+      for (int i = 0; i < n_eff; ++i) {
+        const int wi = w0 - 1 + i;
+        const bool in = wi >= 0;
+        B0[i * stride + tid] = (in && wi * 32 <= m0) ? __ldcs(Rs + (size_t)wi * A + col) : 0u;
+        O[i * stride + tid] = in ? __ldcs(occw + (size_t)wi * A + col) : 0u;
+      }
+    }
+    cluster_sync_all();
+    for (int j = 0; j < kSteps; ++j) {
+      const uint32_t* src = (j & 1) ? B1 : B0;
+      uint32_t* dst = (j & 1) ? B0 : B1;
+      const uint32_t soff = (j & 1) ? planeb : 0u;
+      bool grow = false, hit = false;
+      if (own) {
+        uint32_t prev = 0u, cur = src[tid], dnp = 0u;
+        uint32_t upc = ldc(nb[6] + soff) | ldc(nb[7] + soff) | ldc(nb[8] + soff);
+        for (int i = 0; i < n_eff; ++i) {
+          const uint32_t ro = soff + (uint32_t)i * rowb;
+          const bool more = i + 1 < n_eff;
+          uint32_t nxt = 0u, upn = 0u;
+          if (more) {
+            nxt = src[(i + 1) * stride + tid];
+            upn = ldc(nb[6] + ro + rowb) | ldc(nb[7] + ro + rowb) | ldc(nb[8] + ro + rowb);
+          }
+          const uint32_t dnc = ldc(nb[9] + ro) | ldc(nb[10] + ro) | ldc(nb[11] + ro);
+          // end contacts (tubes t-1, t+1 of the own column), same-layer contacts
+          uint32_t acc = (cur << 1) | (prev >> 31) | (cur >> 1) | (nxt << 31);
+          acc |= ldc(nb[0] + ro) | ldc(nb[1] + ro) | ldc(nb[2] + ro) | ldc(nb[3] + ro) | ldc(nb[4] + ro) |
+                 ldc(nb[5] + ro);
+          // bit b = contact at tube 32 w + b (+1 for up, -1 for down)
+          acc |= __funnelshift_r(upc, upn, sh_up) | __funnelshift_l(dnp, dnc, sh_dn);
+          const uint32_t nw = cur | (acc & O[i * stride + tid]);
+          dst[i * stride + tid] = nw;
+          if (i >= 1 && i <= ivmax) {
+            grow |= nw != cur;
+            if (i == iend) hit |= (((nw & ~cur) >> endb) & 1u) != 0u;
+          }
+          prev = cur; cur = nxt; upc = upn; dnp = dnc;
+        }
+      }
+      if (__any_sync(0xffffffffu, grow) && (tid & 31) == 0) atomicOr(&s_g, 1u << j);
+      if (__any_sync(0xffffffffu, hit) && (tid & 31) == 0) atomicOr(&s_h, 1u << j);
+      cluster_sync_all();
+    }
+    // after an even number of steps the state is back in B0
+    if (own)
+      for (int i = 1; i <= ivmax; ++i) Rd[(size_t)(w0 - 1 + i) * A + col] = B0[i * stride + tid];
+    if (tid == 0) {
+      if (s_g) atomicOr(&x.slot[s].gmask, s_g);
+      if (s_h) atomicOr(&x.slot[s].hmask, s_h);
+      s_g = 0u; s_h = 0u;
+    }
+  }
+  cluster_sync_all();  // no CTA leaves while another may still read its shared memory
+}
+
+// One CTA per slot: the pass's masks -> outputs or the next pass.
+__global__ void __launch_bounds__(kCtlThreads) blocked_control_kernel(BCtx x) {
+  __shared__ int s_n0;
+  __shared__ bool s_last;
+  const int s = blockIdx.x, tid = threadIdx.x;
+  BSlot c = x.slot[s];
+  if (c.phase != BP_EMPTY) {
+    const int A = x.lat.A, L = x.lat.L, TW = x.lat.TW;
+    uint32_t* occw = x.pool + (size_t)s * x.slot_words;
+    uint32_t* R0 = occw + (size_t)TW * A;
+    bool finish = false;
+    int verdict = 0, fh = -1, mstop = 0;
+    if (c.phase == BP_DRAW0) {
+      c.G = c.draws;
+      // m = 0: the metallic sites of layer 0
+      if (tid == 0) s_n0 = 0;
+      __syncthreads();
+      int cnt = 0;
+      for (int a = tid; a < A; a += blockDim.x) {
+        const uint32_t b = occw[a] & 1u;
+        R0[a] = b;
+        cnt += (int)b;
+      }
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if ((tid & 31) == 0 && cnt) atomicAdd(&s_n0, cnt);
+      __syncthreads();
+      if (s_n0 == 0) {
+        finish = true;
+      } else if (L == 1) {
+        finish = true; verdict = 1; fh = 1; mstop = 1;
+      } else {
+        c.phase = BP_STEP; c.m0 = 0; c.par = 0; c.gmask = 0u; c.hmask = 0u;
+      }
+    } else {  // BP_STEP
+      c.G += c.draws;
+      const unsigned g = c.gmask, h = c.hmask;
+      c.gmask = 0u; c.hmask = 0u;
+      // first step of the pass that reached the detector or did not grow
+      const unsigned stop = h | ~g;
+      if (stop) {
+        const int j = __ffs((int)stop) - 1;
+        const int step = c.m0 + 1 + j;
+        finish = true;
+        if ((h >> j) & 1u) { verdict = 1; fh = step + 1; mstop = step + 1; }
+        else mstop = step;
+      } else {
+        c.m0 += kSteps; c.par ^= 1;
+      }
+    }
+    if (tid == 0) {
+      if (finish) {
+        const long long rel = c.item;
+        x.out.verdict[rel] = (uint8_t)verdict;
+        if (x.out.first_hit) x.out.first_hit[rel] = fh;
+        if (x.out.mass) x.out.mass[rel] = 0.f;
+        if (x.out.m_stop) x.out.m_stop[rel] = mstop;
+        if (verdict && x.out.n_perc) atomicAdd(x.out.n_perc, 1ull);
+        atomicAdd(x.n_done, 1ull);
+        take(x, c, atomicAdd(x.work, 1ull));
+      } else {
+        plan_slot(x, c);
+      }
+      x.slot[s] = c;
+    }
+  }
+  // last CTA: prefix of the next pass's items
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(x.arrive, 1u) == (unsigned)(gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  prefix_items(x);
+  if (tid == 0) {
+    *x.arrive = 0u;
+    *x.next_item = 0u;
+    *x.ticks += 1u;
+  }
+}
+
+}  // namespace
+
+struct Shape {
+  int cs = 0, cpr = 0, threads = 0, nrow = 0, smem = 0, clusters = 0;
+};
+
+// Smallest cluster that holds the cross-section (at most 1024 columns per
+// CTA) with a slab of at least 4 valid rows, and that the device can run.
+bool pick_shape(const Lattice& lat, Shape* out) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  const int budget = optin - 64;  // static shared memory of the kernel
+  for (int cs = 1; cs <= 16; cs *= 2) {
+    const int cpr = (lat.A + cs - 1) / cs;
+    if (cpr > kMaxThreads) continue;
+    const int nrow = std::min(kMaxRows, budget / (12 * (cpr + 1)));
+    if (nrow < 6) continue;
+    Shape s;
+    s.cs = cs; s.cpr = cpr; s.threads = (cpr + 31) / 32 * 32; s.nrow = nrow;
+    s.smem = 12 * (cpr + 1) * nrow;
+    if (cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, s.smem) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)cs); cfg.blockDim = dim3((unsigned)s.threads);
+    cfg.dynamicSmemBytes = (size_t)s.smem; cfg.attrs = at; cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, blocked_pass_kernel, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    s.clusters = n;
+    *out = s;
+    return true;
+  }
+  return false;
+}
+
+pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
+  *handled = false;
+  if (!job.bits_only || job.n_cfg <= 0 || std::getenv("PC_BITS_STEPWISE")) return PC_OK;
+  Shape sh;
+  if (!pick_shape(job.lat, &sh)) return PC_OK;  // the step-synchronous solver takes it
+  const Lattice& lat = job.lat;
+  const size_t slot_words = 3 * (size_t)lat.TW * lat.A;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  long long kmax = (long long)(free_b / 2 / (slot_words * 4 + 64));
+  // enough slots that every cluster has slabs to take, as far as memory allows
+  long long K = std::min<long long>(job.n_cfg, std::max(8, 4 * sh.clusters));
+  K = std::min<long long>(K, std::min<long long>(kmax, 4096));
+  if (K < 1) { set_error("verdict-only solver: no memory for one configuration"); return PC_ERR_OOM; }
+
+  const size_t head = 256 + a256_host(sizeof(BSlot) * (size_t)K) + a256_host(4 * (size_t)(K + 1));
+  char* mem = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&mem, head + slot_words * 4 * (size_t)K, st);
+  if (e != cudaSuccess) return cuda_fail(e, "verdict-only solver state");
+  BCtx x;
+  x.lat = lat; x.occ = job.occ; x.occ_bits = job.occ_bits; x.words_per_cfg = job.words_per_cfg;
+  x.n_cfg = job.n_cfg; x.cfg0 = job.cfg0; x.out = job.out; x.K = (int)K;
+  unsigned long long* ctr = (unsigned long long*)mem;
+  x.work = ctr; x.n_done = ctr + 1;
+  x.next_item = (unsigned*)(ctr + 2); x.arrive = x.next_item + 1; x.ticks = x.next_item + 2;
+  x.error = (int*)(x.next_item + 3);
+  x.slot = (BSlot*)(mem + 256);
+  x.pre = (int*)(mem + 256 + a256_host(sizeof(BSlot) * (size_t)K));
+  x.pool = (uint32_t*)(mem + head);
+  x.slot_words = slot_words;
+  x.cpr = sh.cpr; x.nrow = sh.nrow; x.nw = sh.nrow - 2;
+
+  pc_status rc = PC_OK;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)sh.cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(sh.cs * sh.clusters)); cfg.blockDim = dim3((unsigned)sh.threads);
+  cfg.dynamicSmemBytes = (size_t)sh.smem; cfg.stream = st; cfg.attrs = at; cfg.numAttrs = 1;
+  // a configuration needs at most (sites / 32 + 2) passes: the reached set
+  // grows by at least one site per step until it stops
+  const long long per_cfg = (long long)(lat.N / kSteps) + 3;
+  const long long rounds = (job.n_cfg + K - 1) / K;
+  const unsigned long long max_ticks = (unsigned long long)std::min<long long>(per_cfg * rounds, 1ll << 40);
+  unsigned long long* done_h = nullptr;
+  e = cudaMallocHost((void**)&done_h, sizeof(unsigned long long));
+  if (e != cudaSuccess) { cudaFreeAsync(mem, st); return cuda_fail(e, "pinned count"); }
+  *done_h = 0;
+  blocked_init_kernel<<<1, 256, 0, st>>>(x);
+  e = cudaGetLastError();
+  unsigned long long ticks = 0;
+  while (e == cudaSuccess && *done_h < (unsigned long long)job.n_cfg) {
+    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) {
+      e = cudaLaunchKernelEx(&cfg, blocked_pass_kernel, x);
+      if (e == cudaSuccess) {
+        blocked_control_kernel<<<x.K, kCtlThreads, 0, st>>>(x);
+        e = cudaGetLastError();
+      }
+    }
+    ticks += kChunk;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(done_h, x.n_done, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ticks > max_ticks && *done_h < (unsigned long long)job.n_cfg) {
+      set_error("verdict-only solver did not converge");
+      rc = PC_ERR_INTERNAL;
+      break;
+    }
+  }
+  if (e != cudaSuccess) rc = cuda_fail(e, "verdict-only solver");
+  cudaFreeHost(done_h);
+  cudaFreeAsync(mem, st);
+  *handled = true;
+  return rc;
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_bits_blocked_shape(int32_t W, int32_t* cluster_size, int32_t* columns_per_cta,
+                                           int32_t* slab_rows, int32_t* clusters) {
+  if (W < 0 || W > 255) { pc::set_error("pc_bits_blocked_shape: W must be in [0, 255]"); return PC_ERR_ARG; }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return pc::cuda_fail(e, "pc_bits_blocked_shape");
+  pc::Lattice lat{};
+  lat.W = W; lat.A = 3 * W * (W + 1) + 1;
+  pc::Shape s;
+  if (!pc::pick_shape(lat, &s)) {
+    pc::set_error("pc_bits_blocked_shape: no cluster of this device holds the cross-section");
+    return PC_ERR_ARG;
+  }
+  if (cluster_size) *cluster_size = s.cs;
+  if (columns_per_cta) *columns_per_cta = s.cpr;
+  if (slab_rows) *slab_rows = s.nrow;
+  if (clusters) *clusters = s.clusters;
+  return PC_OK;
+}

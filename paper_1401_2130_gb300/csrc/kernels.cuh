@@ -85,6 +85,10 @@ int* stream_plan_error(StreamPlan* P);
 void stream_plan_release(StreamPlan* P, cudaStream_t st);
 size_t stream_slot_bytes(int W, int L);
 pc_status run_stream(const StreamJob& job, cudaStream_t st);
+// Verdict-only solver with temporal blocking (blocked.cu): runs a PC_BITS_ONLY
+// job when a thread-block cluster holds the lattice's cross-section
+// (*handled = true), else leaves it to the step-synchronous solver.
+pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled);
 
 // Server engine (stream.cu): streamed-solver slots bound to queries by the host.
 struct ServerEngine;

@@ -1190,6 +1190,11 @@ pc_status server_engine_status(ServerEngine* E, cudaStream_t st, int buf, const 
 // ordered; no host synchronisation).
 pc_status run_stream(const StreamJob& job, cudaStream_t st) {
   if (job.n_cfg <= 0) return PC_OK;
+  if (job.bits_only) {  // verdict only: 32 steps per visit of a slab where a cluster holds the lattice
+    bool handled = false;
+    const pc_status rb = run_blocked(job, st, &handled);
+    if (handled || rb != PC_OK) return rb;
+  }
   StreamQuery q;
   q.lat = job.lat; q.occ = job.occ; q.occ_bits = job.occ_bits; q.words_per_cfg = job.words_per_cfg;
   q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out; q.bits_only = job.bits_only;
