@@ -51,8 +51,8 @@ namespace pc {
 namespace {
 
 constexpr int kSteps = 32;       // steps per pass (one word row of halo on each side)
-constexpr int kMaxThreads = 1024;
-constexpr int kMaxRows = 34;     // slab rows in shared memory (valid rows + 2 halo rows)
+constexpr int kMaxThreads = 800;  // columns per CTA: 80 registers a thread
+constexpr int kMaxQuads = 9;      // slab rows / 4 in shared memory (valid rows + 2 halo rows)
 constexpr int kCtlThreads = 256;
 constexpr int kChunk = 16;       // ticks launched between reads of the completion count
 
@@ -189,8 +189,38 @@ __global__ void blocked_init_kernel(BCtx x) {
   }
 }
 
+__device__ __forceinline__ uint4 ldc4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint4 lds4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t lds_r(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 or4(uint4 a, uint4 b) { return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w); }
+__device__ __forceinline__ uint32_t q_at(const uint4& v, int r) { return r == 0 ? v.x : r == 1 ? v.y : r == 2 ? v.z : v.w; }
+
 // One pass: every slab of every active slot (32 steps each) and the rows to
 // draw.  Grid = whole clusters, persistent; items are taken cluster-wide.
+//
+// Shared memory of a CTA: three arrays (reached set, buffers 0 and 1, and
+// occupancy), each [quad][column] of 16 bytes: slab rows 4k .. 4k+3 of a
+// column side by side, so one 128-bit load brings four rows of a contact and
+// a warp's 32 columns stay one contiguous run (distributed shared memory is
+// served in 32-byte sectors).
 __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int s_item[2];
@@ -198,38 +228,38 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const uint32_t rank = cluster_rank();
   const int A = x.lat.A, L = x.lat.L, TW = x.lat.TW;
-  const int stride = x.cpr + 1;       // words per slab row
-  const int plane = x.nrow * stride;  // words per array
-  uint32_t* B0 = sm;
-  uint32_t* B1 = sm + plane;
-  uint32_t* O = sm + 2 * plane;
+  const int stride = x.cpr + 1;                 // columns per quad row (column cpr: zero)
+  const int nq = x.nrow >> 2;                   // quads per array
+  const uint32_t qrow = (uint32_t)stride * 16u;  // bytes per quad row
+  const uint32_t arr = (uint32_t)nq * qrow;      // bytes per array
   const int c0 = (int)rank * x.cpr;
   const int ncol = max(0, min(x.cpr, A - c0));
-  for (int i = tid; i < 3 * x.nrow; i += nt) sm[i * stride + x.cpr] = 0u;  // zero column
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm);
+  for (int i = tid; i < 3 * nq; i += nt) sts4(base + (uint32_t)i * qrow + (uint32_t)x.cpr * 16u, make_uint4(0, 0, 0, 0));
   if (tid == 0) { s_g = 0u; s_h = 0u; }
-  // cluster addresses of this column's contacts in row 0 of B0 (a contact
-  // outside the hexagon reads the zero column)
   const bool own = tid < ncol;
   const int col = c0 + tid;
-  uint32_t nb[kLateral];
+  const uint32_t me = base + (uint32_t)(own ? tid : x.cpr) * 16u;  // quad 0 of this column, buffer 0
+  uint32_t nb[kLateral];  // cluster addresses of the contacts' quad 0, buffer 0
   int sg = 0;
   if (own) {
     sg = x.lat.sigma[col];
 #pragma unroll
     for (int d = 0; d < kLateral; ++d) {
+      // a contact outside the hexagon reads the zero column
       const int j = x.lat.nbr[col * kLateral + d];
       const int r = j >= A ? (int)rank : j / x.cpr;
       const int l = j >= A ? x.cpr : j - r * x.cpr;
-      nb[d] = map_rank(B0 + l, (uint32_t)r);
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(nb[d]) : "r"(base + (uint32_t)l * 16u), "r"((uint32_t)r));
     }
   } else {
 #pragma unroll
-    for (int d = 0; d < kLateral; ++d) nb[d] = 0u;
+    for (int d = 0; d < kLateral; ++d)
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(nb[d]) : "r"(me), "r"(rank));
   }
   // the up contacts reach tube t+1 from sigma = 2, the down contacts tube t-1
   // from sigma = 0: one funnel shift of their ORed words
   const uint32_t sh_up = sg == 2 ? 1u : 0u, sh_dn = sg == 0 ? 1u : 0u;
-  const uint32_t planeb = (uint32_t)plane * 4u, rowb = (uint32_t)stride * 4u;
   const int endw = (L - 1) >> 5, endb = (L - 1) & 31;
   const uint32_t item_addr = map_rank(&s_item[0], 0u);
   cluster_sync_all();
@@ -247,13 +277,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
     const int s = lo;
     const BSlot c = x.slot[s];
     const int local = item - x.pre[s];
-    uint32_t* occw = x.pool + (size_t)s * x.slot_words;
-    uint32_t* R0 = occw + (size_t)TW * A;
-    uint32_t* R1 = R0 + (size_t)TW * A;
+    // slot arrays: occupancy, then the reached-set buffers R0 and R1
+    const size_t plane = (size_t)TW * A;
 
     if (local >= c.tiles) {  // one row of occupancy for the next pass
       const int tw = c.G + (local - c.tiles);
-      if (own) occw[(size_t)tw * A + col] = draw_word(x, c.item, tw, col);
+      if (own) x.pool[(size_t)s * x.slot_words + (size_t)tw * A + col] = draw_word(x, c.item, tw, col);
       continue;
     }
 
@@ -262,58 +291,91 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
     const int m0 = c.m0;
     const int rtop = min((m0 + kSteps) >> 5, TW - 1);
     const int n_eff = min(x.nrow, rtop - w0 + 2);  // rows above rtop stay empty for 32 steps
+    const int q_eff = (n_eff + 3) >> 2;            // quads computed (rows past n_eff loaded as zero)
     const int ivmax = min(x.nw, n_eff - 1);        // valid rows 1 .. ivmax
     const int iend = endw - (w0 - 1);
-    const uint32_t* Rs = c.par ? R1 : R0;
-    uint32_t* Rd = c.par ? R0 : R1;
+    const bool end_here = iend >= 1 && iend <= ivmax;
     if (own) {
-      for (int i = 0; i < n_eff; ++i) {
-        const int wi = w0 - 1 + i;
-        const bool in = wi >= 0;
-        B0[i * stride + tid] = (in && wi * 32 <= m0) ? __ldcs(Rs + (size_t)wi * A + col) : 0u;
-        O[i * stride + tid] = in ? __ldcs(occw + (size_t)wi * A + col) : 0u;
+      const uint32_t* occw = x.pool + (size_t)s * x.slot_words;
+      const uint32_t* Rs = occw + plane * (size_t)(1 + c.par);
+      for (int k = 0; k < q_eff; ++k) {
+        uint32_t rv[4], ov[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int i = 4 * k + r, wi = w0 - 1 + i;
+          const bool in = wi >= 0 && i < n_eff;
+          rv[r] = (in && wi * 32 <= m0) ? __ldcs(Rs + (size_t)wi * A + col) : 0u;
+          ov[r] = in ? __ldcs(occw + (size_t)wi * A + col) : 0u;
+        }
+        sts4(me + (uint32_t)k * qrow, make_uint4(rv[0], rv[1], rv[2], rv[3]));
+        sts4(me + 2u * arr + (uint32_t)k * qrow, make_uint4(ov[0], ov[1], ov[2], ov[3]));
       }
     }
     cluster_sync_all();
     for (int j = 0; j < kSteps; ++j) {
-      const uint32_t* src = (j & 1) ? B1 : B0;
-      uint32_t* dst = (j & 1) ? B0 : B1;
-      const uint32_t soff = (j & 1) ? planeb : 0u;
+      const uint32_t so = (j & 1) ? arr : 0u, dso = (j & 1) ? 0u : arr;
       bool grow = false, hit = false;
       if (own) {
-        uint32_t prev = 0u, cur = src[tid], dnp = 0u;
-        uint32_t upc = ldc(nb[6] + soff) | ldc(nb[7] + soff) | ldc(nb[8] + soff);
-        for (int i = 0; i < n_eff; ++i) {
-          const uint32_t ro = soff + (uint32_t)i * rowb;
-          const bool more = i + 1 < n_eff;
-          uint32_t nxt = 0u, upn = 0u;
-          if (more) {
-            nxt = src[(i + 1) * stride + tid];
-            upn = ldc(nb[6] + ro + rowb) | ldc(nb[7] + ro + rowb) | ldc(nb[8] + ro + rowb);
+        uint32_t diff = 0u, prevw = 0u, dnl = 0u;
+        uint4 cur = lds4(me + so);
+        uint4 upc = or4(or4(ldc4(nb[6] + so), ldc4(nb[7] + so)), ldc4(nb[8] + so));
+        for (int k = 0; k < q_eff; ++k) {
+          const uint32_t ko = so + (uint32_t)k * qrow;
+          uint4 ownn = make_uint4(0, 0, 0, 0), upn = make_uint4(0, 0, 0, 0);
+          if (k + 1 < q_eff) {
+            ownn = lds4(me + ko + qrow);
+            upn = ldc4(nb[6] + ko + qrow);
+            upn = or4(upn, ldc4(nb[7] + ko + qrow));
+            upn = or4(upn, ldc4(nb[8] + ko + qrow));
           }
-          const uint32_t dnc = ldc(nb[9] + ro) | ldc(nb[10] + ro) | ldc(nb[11] + ro);
-          // end contacts (tubes t-1, t+1 of the own column), same-layer contacts
-          uint32_t acc = (cur << 1) | (prev >> 31) | (cur >> 1) | (nxt << 31);
-          acc |= ldc(nb[0] + ro) | ldc(nb[1] + ro) | ldc(nb[2] + ro) | ldc(nb[3] + ro) | ldc(nb[4] + ro) |
-                 ldc(nb[5] + ro);
-          // bit b = contact at tube 32 w + b (+1 for up, -1 for down)
-          acc |= __funnelshift_r(upc, upn, sh_up) | __funnelshift_l(dnp, dnc, sh_dn);
-          const uint32_t nw = cur | (acc & O[i * stride + tid]);
-          dst[i * stride + tid] = nw;
-          if (i >= 1 && i <= ivmax) {
-            grow |= nw != cur;
-            if (i == iend) hit |= (((nw & ~cur) >> endb) & 1u) != 0u;
+          uint4 dn = ldc4(nb[9] + ko);
+          dn = or4(dn, ldc4(nb[10] + ko));
+          dn = or4(dn, ldc4(nb[11] + ko));
+          uint4 sl = ldc4(nb[0] + ko);
+          sl = or4(sl, ldc4(nb[1] + ko));
+          sl = or4(sl, ldc4(nb[2] + ko));
+          sl = or4(sl, ldc4(nb[3] + ko));
+          sl = or4(sl, ldc4(nb[4] + ko));
+          sl = or4(sl, ldc4(nb[5] + ko));
+          const uint4 oc = lds4(me + 2u * arr + (uint32_t)k * qrow);
+          // rows of this quad that are valid (slab rows 1 .. ivmax)
+          const int i0 = 4 * k;
+          uint32_t out[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const uint32_t cw = q_at(cur, r);
+            const uint32_t pw = r == 0 ? prevw : q_at(cur, r - 1);
+            const uint32_t nw = r == 3 ? ownn.x : q_at(cur, r + 1);
+            const uint32_t uh = r == 3 ? upn.x : q_at(upc, r + 1);
+            const uint32_t dl = r == 0 ? dnl : q_at(dn, r - 1);
+            // end contacts (tubes t-1, t+1), same-layer contacts, and the up /
+            // down contacts at tube t+1 (sigma = 2) / t-1 (sigma = 0)
+            uint32_t acc = __funnelshift_l(pw, cw, 1) | __funnelshift_r(cw, nw, 1) | q_at(sl, r);
+            acc |= __funnelshift_r(q_at(upc, r), uh, sh_up) | __funnelshift_l(dl, q_at(dn, r), sh_dn);
+            out[r] = cw | (acc & q_at(oc, r));
+            const int i = i0 + r;
+            if (i >= 1 && i <= ivmax) diff |= out[r] ^ cw;
           }
-          prev = cur; cur = nxt; upc = upn; dnp = dnc;
+          sts4(me + dso + (uint32_t)k * qrow, make_uint4(out[0], out[1], out[2], out[3]));
+          prevw = cur.w; dnl = dn.w; cur = ownn; upc = upn;
+        }
+        grow = diff != 0u;
+        if (end_here) {  // the detector layer's word, before and after
+          const uint32_t off = (uint32_t)(iend >> 2) * qrow + 4u * (uint32_t)(iend & 3);
+          const uint32_t a = lds_r(me + so + off), b = lds_r(me + dso + off);
+          hit = (((b & ~a) >> endb) & 1u) != 0u;
         }
       }
       if (__any_sync(0xffffffffu, grow) && (tid & 31) == 0) atomicOr(&s_g, 1u << j);
       if (__any_sync(0xffffffffu, hit) && (tid & 31) == 0) atomicOr(&s_h, 1u << j);
       cluster_sync_all();
     }
-    // after an even number of steps the state is back in B0
-    if (own)
-      for (int i = 1; i <= ivmax; ++i) Rd[(size_t)(w0 - 1 + i) * A + col] = B0[i * stride + tid];
+    // after an even number of steps the state is back in buffer 0
+    if (own) {
+      uint32_t* Rd = x.pool + (size_t)s * x.slot_words + plane * (size_t)(2 - c.par);
+      for (int i = 1; i <= ivmax; ++i)
+        Rd[(size_t)(w0 - 1 + i) * A + col] = lds_r(me + (uint32_t)(i >> 2) * qrow + 4u * (uint32_t)(i & 3));
+    }
     if (tid == 0) {
       if (s_g) atomicOr(&x.slot[s].gmask, s_g);
       if (s_h) atomicOr(&x.slot[s].hmask, s_h);
@@ -409,24 +471,25 @@ struct Shape {
   int cs = 0, cpr = 0, threads = 0, nrow = 0, smem = 0, clusters = 0;
 };
 
-// Smallest cluster that holds the cross-section (at most 1024 columns per
-// CTA) with a slab of at least 4 valid rows, and that the device can run.
+// Smallest cluster that holds the cross-section (at most 800 columns per
+// CTA) with a slab of at least 3 quads (12 rows, 10 valid), and that the
+// device can run.
 bool pick_shape(const Lattice& lat, Shape* out) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
   const int budget = optin - 64;  // static shared memory of the kernel
+  if (cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    cudaGetLastError();
   for (int cs = 1; cs <= 16; cs *= 2) {
     const int cpr = (lat.A + cs - 1) / cs;
     if (cpr > kMaxThreads) continue;
-    const int nrow = std::min(kMaxRows, budget / (12 * (cpr + 1)));
-    if (nrow < 6) continue;
+    const int nq = std::min(kMaxQuads, budget / (48 * (cpr + 1)));
+    if (nq < 3) continue;
     Shape s;
-    s.cs = cs; s.cpr = cpr; s.threads = (cpr + 31) / 32 * 32; s.nrow = nrow;
-    s.smem = 12 * (cpr + 1) * nrow;
-    if (cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, s.smem) != cudaSuccess ||
-        (cs > 8 && cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                       cudaSuccess)) {
+    s.cs = cs; s.cpr = cpr; s.threads = (cpr + 31) / 32 * 32; s.nrow = 4 * nq;
+    s.smem = 48 * (cpr + 1) * nq;
+    if (cudaFuncSetAttribute(blocked_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, s.smem) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }

@@ -38,16 +38,16 @@ def _stepwise(*args, **kw):
         del os.environ["PC_BITS_STEPWISE"]
 
 
-@pytest.mark.parametrize("W,cs", [(0, 1), (12, 1), (17, 1), (18, 2), (32, 4), (64, 16)])
+@pytest.mark.parametrize("W,cs", [(0, 1), (12, 1), (15, 1), (16, 2), (32, 4), (64, 16)])
 def test_cluster_shape(W, cs):
-    """Columns per CTA = ceil(A / cluster size) <= 1024: the smallest cluster
-    that holds the cross-section (A = 3W(W+1)+1 columns)."""
+    """Columns per CTA = ceil(A / cluster size) <= 800 (one per thread): the
+    smallest cluster that holds the cross-section (A = 3W(W+1)+1 columns)."""
     s = pc.pc_bits_blocked_shape(W)
     assert s is not None, W
     A = 3 * W * (W + 1) + 1
     assert s["cluster_size"] == cs
-    assert s["columns_per_cta"] == -(-A // cs) <= 1024
-    assert 6 <= s["slab_rows"] <= 34 and s["clusters"] >= 1
+    assert s["columns_per_cta"] == -(-A // cs) <= 800
+    assert s["slab_rows"] % 4 == 0 and 12 <= s["slab_rows"] <= 36 and s["clusters"] >= 1
 
 
 @pytest.mark.parametrize("W,L,p,seed,cfg0,n", [
