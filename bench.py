@@ -277,16 +277,38 @@ HBM_BYTES_PER_SU = 8.375
 # DRAM bytes (read + write) measured with ncu on the current kernels, to be
 # re-measured whenever they change: the resident kernel per p-sweep launch
 # (tables and outputs only), and the streamed sweep per site-update
-# (controlled capture of the large lattice with 4 active slots, tick 600:
-# 4 x 12,481 columns x 600 layers)
+# (controlled capture of the large lattice with 4 active slots, ticks
+# 600..631 -- one period of the word-row preparation -- i.e. steps 599..630:
+# 4 x 12,481 columns x (600 + ... + 631) layers)
 RESIDENT_DRAM_BYTES_PER_LAUNCH = 81152.0  # p = 0.2, 2,000 configurations
-SWEEP_DRAM_BYTES_PER_SU = (173.08e6 + 97.65e6) / 29.95e6
+SWEEP_DRAM_BYTES_PER_SU = (5688.3e6 + 2947.8e6) / (4 * 12481 * 32 * (600 + 631) / 2)
 # bits-only variant: occupancy 1/8 B + reached-set bit read and write 1/4 B
 BITS_BYTES_PER_SU = 0.375
+# The verdict-only solver with temporal blocking keeps a slab on chip for 32
+# steps: measured DRAM bytes per site-update of its pass kernel (controlled
+# capture: 4 slots at p = 0.17, pass of steps 1889..1920, 24.80 MB for
+# 4 x 12,481 x (1890 + ... + 1921) site-updates), and its shared-memory bytes
+# per site-update (each 32-tube word step loads the column's next word, its
+# occupancy word and its 12 contacts' words, and stores one word: 60 B / 32)
+BLOCKED_DRAM_BYTES_PER_SU = 24.80e6 / (4 * 12481 * 32 * (1890 + 1921) / 2)
+BLOCKED_SMEM_BYTES_PER_SU = 60 / 32
+BLOCKED_CHUNK = 16  # ticks the host launches between reads of the completion count
 
 
 def batching_specs(n=10_000):
     return [(Wb, Wb * r, 0.1533, 3, 0, n) for Wb in (4, 8, 16, 32) for r in (1, 2, 4, 8, 16, 32, 64)]
+
+
+def blocked_launches(verdict, first_hit, m_stop) -> int:
+    """Kernels of one verdict-only solve by the blocked solver whose
+    configurations all hold a slot at once: the init kernel, then a pass and a
+    control kernel per tick, launched in chunks; one tick draws the first
+    rows, then one tick per 32 steps of the longest configuration."""
+    v = np.asarray(verdict) != 0
+    last = np.where(v, np.asarray(first_hit) - 1, np.asarray(m_stop))  # terminating step (0: none)
+    passes = np.where(last >= 1, (last - 1) // 32 + 1, 0)
+    ticks = 1 + int(passes.max(initial=0))
+    return 1 + 2 * BLOCKED_CHUNK * (-(-ticks // BLOCKED_CHUNK))
 
 
 def solve_ticks(verdict, first_hit, m_stop) -> int:
@@ -304,6 +326,10 @@ def run_large(args, pc, torch, rank, world, local, dist):
     ps = list(LPS) if args.large_p is None else [float(v) for v in args.large_p.split(",")]
     n = args.large_configs
     block = max(1, min(args.large_block, n))
+    # verdict-only solves run 32 steps per visit of a slab held by one
+    # thread-block cluster (PC_BITS_STEPWISE=1 keeps the step-synchronous path)
+    shape = pc.pc_bits_blocked_shape(LW) if args.bits_only else None
+    blocked = shape is not None and not os.environ.get("PC_BITS_STEPWISE")
     nb = max(1, n // block)
     base = rank * n  # weak scaling: rank r owns configurations [r n, (r + 1) n) at every p
     stream = torch.cuda.current_stream()
@@ -357,6 +383,14 @@ def run_large(args, pc, torch, rank, world, local, dist):
         return sum(solve_ticks(host[p]["verdict"][sl], host[p]["first_hit"][sl], host[p]["m_stop"][sl])
                    for p in ps)
 
+    def block_launches(b):
+        sl = slice(b * block, (b + 1) * block)
+        if blocked:
+            return sum(blocked_launches(host[p]["verdict"][sl], host[p]["first_hit"][sl], host[p]["m_stop"][sl])
+                       for p in ps)
+        # query upload and init, then a sweep and a control kernel per tick
+        return block_ticks(b) * 2 + 2 * len(ps)
+
     su_rank = sum(block_su(b) for b in blocks)
     t_rank = float(sum(times))
     su_all, t_max = su_rank, t_rank
@@ -395,7 +429,9 @@ def run_large(args, pc, torch, rank, world, local, dist):
     # per step of this rank (the unit the events time): algorithmic bytes / time
     achieved = bps * su_rank / t_rank / 1e9
     traffic = None
-    if not args.bits_only and SWEEP_DRAM_BYTES_PER_SU is not None:
+    if blocked:
+        traffic = BLOCKED_DRAM_BYTES_PER_SU * su_rank / len(times)
+    elif not args.bits_only and SWEEP_DRAM_BYTES_PER_SU is not None:
         traffic = SWEEP_DRAM_BYTES_PER_SU * su_rank / len(times)
     perc = {str(p): int(host[p]["verdict"][:len(set(blocks)) * block].sum()) for p in ps}
     line = {
@@ -407,25 +443,40 @@ def run_large(args, pc, torch, rank, world, local, dist):
                    "W": LW, "L": LL, "configs_per_p": n, "configs_per_step": block * len(ps) * world,
                    "step": f"configurations [{block}b, {block}b + {block}) at each p, b = step mod {nb}",
                    "site_updates_per_step": su_all / len(times), "percolating_per_p": perc,
-                   "solver": "streamed", "parallelism": f"configs sharded over {world} GPU(s)",
+                   "solver": (f"verdict-only, temporally blocked: 32 steps per slab of "
+                              f"{shape['slab_rows'] - 2} word rows, clusters of {shape['cluster_size']} CTAs "
+                              f"({shape['clusters']} resident)" if blocked else "streamed"),
+                   "parallelism": f"configs sharded over {world} GPU(s)",
                    "l2": "inputs larger than L2 (each configuration's state is ~0.5 GB), no flush"},
         "configs_per_s": block * len(ps) * world * len(times) / t_max,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "traffic_note": "ncu DRAM bytes (read + write) per site-update of sweep_kernel "
-                                     "(controlled capture, all slots active) x the step's site-updates",
+                     "traffic_note": ("ncu DRAM bytes (read + write) per site-update of "
+                                      + ("blocked_pass_kernel (controlled capture, 4 slots)" if blocked else
+                                         "sweep_kernel (controlled capture, all slots active)")
+                                      + " x the step's site-updates"),
                      "model": f"{bps} B/site-update x site-updates of a step / CUDA-event time of the "
                               "step (every kernel of the solve), peak = measured copy bandwidth "
                               "(MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clk.summary(),
         "e2e": {"value": su_e2e / e2e_t if e2e_steps else None, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": len(ps) * (block * (1 + 4 + 4 + 4) + 8)},
-        # kernels of each solve: query upload and init, then a sweep and a
-        # control kernel per tick
-        "gpu_launches": sum(block_ticks(b) * 2 + 2 * len(ps) for b in blocks),
+        "gpu_launches": sum(block_launches(b) for b in blocks),
         "step_ms": [round(t * 1e3, 3) for t in times],
         "wall_s_timed": wall,
     }
+    if blocked:
+        # the step-synchronous model's bytes do not reach DRAM here: the slab
+        # stays in shared memory for 32 steps, so shared memory bounds it
+        smem_peak = 152 * 128 * (line["clocks"].get("sm_mhz") or 2070.0) * 1e6 / 1e9
+        ach = BLOCKED_SMEM_BYTES_PER_SU * su_rank / t_rank / 1e9
+        line["roofline_onchip"] = {
+            "bound": "smem", "achieved": ach, "peak": smem_peak, "unit": "GB/s", "frac": ach / smem_peak,
+            "model": f"{BLOCKED_SMEM_BYTES_PER_SU} B of shared-memory traffic per site-update (12 contact "
+                     "words, the next own word and the occupancy word loaded, one word stored per 32-tube "
+                     "word step); peak = 152 SMs x 128 B/clock x the median SM clock (derived, not "
+                     f"measured); {shape['clusters']} clusters of {shape['cluster_size']} CTAs occupy "
+                     f"{shape['clusters'] * shape['cluster_size']} SMs"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], line["parity"] = large_cpu_leg(args, host, ps, block, sorted(set(blocks)))
     return line

@@ -353,9 +353,10 @@ pc_status pc_stream_layout(int32_t W, int32_t* P, int32_t* s_begin, int32_t* n_s
  * 1..16), columns_per_cta (cross-section columns each CTA owns, one per
  * thread, at most 800), slab_rows (32-tube word rows per slab in shared
  * memory, the valid rows plus one halo row above and one below: a multiple
- * of 4 from 12 to 36), clusters (clusters the device runs at once).  Errors: PC_ERR_ARG (W outside [0, 255], or no cluster of
- * this device holds the cross-section -- the step-synchronous solver then
- * runs such inspections), PC_ERR_CUDA (no device).
+ * of 4 from 12 to 36), clusters (clusters the device runs at once).
+ * Errors: PC_ERR_ARG (W outside [0, 255], or no cluster of this device holds
+ * the cross-section -- the step-synchronous solver then runs such
+ * inspections), PC_ERR_CUDA (no device).
  */
 pc_status pc_bits_blocked_shape(int32_t W, int32_t* cluster_size, int32_t* columns_per_cta,
                                 int32_t* slab_rows, int32_t* clusters);
