@@ -164,12 +164,14 @@ __device__ inline void take(const BCtx& x, BSlot& c, unsigned long long item) {
   plan_slot(x, c);
 }
 
+// Other CTAs wrote the slot records: they are read through L2 (__ldcg), not
+// from a line this SM's L1 may hold from before.
 __device__ void prefix_items(const BCtx& x) {
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int s = 0; s < x.K; ++s) {
       x.pre[s] = acc;
-      acc += x.slot[s].tiles + x.slot[s].draws;
+      acc += __ldcg(&x.slot[s].tiles) + __ldcg(&x.slot[s].draws);
     }
     x.pre[x.K] = acc;
   }
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
 
     if (local >= c.tiles) {  // one row of occupancy for the next pass
       const int tw = c.G + (local - c.tiles);
-      if (own) x.pool[(size_t)s * x.slot_words + (size_t)tw * A + col] = draw_word(x, c.item, tw, col);
+      if (own && tw < TW) x.pool[(size_t)s * x.slot_words + (size_t)tw * A + col] = draw_word(x, c.item, tw, col);
       continue;
     }
 
