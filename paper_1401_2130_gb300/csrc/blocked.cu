@@ -16,12 +16,15 @@
 // and below the slab, which 32 steps cannot cross.
 //
 // Slab ("tile") of a pass: valid word rows [w0, w0 + nw) plus the halo rows
-// w0 - 1 and w0 + nw, in shared memory as rows x (cpr + 1) words (column
-// cpr is the always-zero stand-in for contacts outside the hexagon), with
-// the occupancy words beside them.  Each step reads a column's own words,
-// its six same-layer contacts and the three up / three down contacts of the
-// neighbouring rows from the owning CTA's shared memory (ld.shared::cluster),
-// writes the new words to the other buffer, and ends with a cluster barrier.
+// w0 - 1 and w0 + nw, in shared memory as quads: rows 4k .. 4k+3 of a column
+// side by side in 16 bytes, [quad][cpr + 1] per array (entry cpr is the
+// always-zero stand-in for contacts outside the hexagon), for the two
+// reached-set buffers and the occupancy.  Each step reads a column's own
+// words, its six same-layer contacts and the three up / three down contacts
+// four rows at a time from the owning CTA's shared memory
+// (ld.shared::cluster.v4: a warp's 32 columns stay one contiguous run, as
+// distributed shared memory is served in 32-byte sectors), writes the new
+// words to the other buffer, and ends with a cluster barrier.
 // A step's growth and detector hit are ORed, per step, into a 32-bit mask of
 // the configuration; valid rows of different slabs partition the layers, so
 // the masks are exact.  After the pass the control kernel takes the first
@@ -88,8 +91,7 @@ struct BCtx {
   unsigned long long* n_done;
   unsigned* next_item;
   unsigned* arrive;
-  unsigned* ticks;
-  int* error;
+  unsigned* ticks;             // passes run (diagnostics)
   int cpr;                     // columns per CTA of a cluster
   int nrow;                    // slab rows in shared memory
   int nw;                      // valid rows per slab (nrow - 2)
@@ -538,7 +540,6 @@ pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   unsigned long long* ctr = (unsigned long long*)mem;
   x.work = ctr; x.n_done = ctr + 1;
   x.next_item = (unsigned*)(ctr + 2); x.arrive = x.next_item + 1; x.ticks = x.next_item + 2;
-  x.error = (int*)(x.next_item + 3);
   x.slot = (BSlot*)(mem + 256);
   x.pre = (int*)(mem + 256 + a256_host(sizeof(BSlot) * (size_t)K));
   x.pool = (uint32_t*)(mem + head);
