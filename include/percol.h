@@ -82,10 +82,14 @@ typedef int32_t pc_status;
                                   Sec. II.B), so the reached set decides every
                                   configuration first and the FP32 recursion
                                   then runs, for exactly first_hit - 1 steps,
-                                  on the percolating ones only.  Applies to the
-                                  resident solver; the streamed solver accepts
-                                  the flag and runs its single pass.  Ignored
-                                  with PC_BITS_ONLY */
+                                  on the percolating ones only.  In pc_inspect
+                                  and pc_inspect_occupancy both solvers apply
+                                  it; on the streamed path the call waits for
+                                  the verdicts before it starts the FP32
+                                  solves (it synchronises cuda_stream even with
+                                  PC_OUT_DEVICE).  pc_batch_run's streamed
+                                  queries run their single pass.  Ignored with
+                                  PC_BITS_ONLY */
 
 /*
  * Lattice size (Sec. II.A): n_columns = A = 3W(W+1)+1, n_sites = A*L.

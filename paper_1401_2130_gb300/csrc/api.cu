@@ -161,7 +161,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       j.out.m_stop = s.m_stop; j.out.n_perc = s.n_perc;
       j.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
       j.error_out = (int*)(s.work + 2);
-      rc = run_stream(j, st);
+      rc = (!j.bits_only && (flags & PC_VERDICT_FIRST)) ? run_stream_verdict_first(j, st) : run_stream(j, st);
     }
     if (rc) break;
     if (!dev_out) {

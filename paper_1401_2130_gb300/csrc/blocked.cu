@@ -517,7 +517,7 @@ bool pick_shape(const Lattice& lat, Shape* out) {
 
 pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   *handled = false;
-  if (!job.bits_only || job.n_cfg <= 0 || std::getenv("PC_BITS_STEPWISE")) return PC_OK;
+  if (!job.bits_only || job.sel || job.n_cfg <= 0 || std::getenv("PC_BITS_STEPWISE")) return PC_OK;
   Shape sh;
   if (!pick_shape(job.lat, &sh)) return PC_OK;  // the step-synchronous solver takes it
   const Lattice& lat = job.lat;

@@ -71,6 +71,9 @@ struct StreamQuery {
   uint32_t cfg0;
   Outputs out;
   int bits_only = 0;  // reached set only: no FP units, mass written 0
+  // device list of n_cfg configurations (indices from 0 within the query) to
+  // solve, outputs written at those indices; null = configurations 0..n_cfg-1
+  const int64_t* sel = nullptr;
 };
 struct StreamJob : StreamQuery {
   int* error_out = nullptr;  // device int: 1 if the tick bound was hit
@@ -85,6 +88,10 @@ int* stream_plan_error(StreamPlan* P);
 void stream_plan_release(StreamPlan* P, cudaStream_t st);
 size_t stream_slot_bytes(int W, int L);
 pc_status run_stream(const StreamJob& job, cudaStream_t st);
+// PC_VERDICT_FIRST on the streamed path: a verdict-only solve of every
+// configuration, then the full solve of the percolating ones (the host waits
+// for the first to count them).
+pc_status run_stream_verdict_first(const StreamJob& job, cudaStream_t st);
 // Verdict-only solver with temporal blocking (blocked.cu): runs a PC_BITS_ONLY
 // job when a thread-block cluster holds the lattice's cross-section
 // (*handled = true), else leaves it to the step-synchronous solver.

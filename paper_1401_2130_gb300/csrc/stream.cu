@@ -78,7 +78,11 @@ struct QDev {
   Outputs out;
   long long item0;  // first global work item of this query
   int bits_only;    // reached set only: no FP units, mass written 0
+  const int64_t* sel;  // item i of the query solves configuration sel[i] (null: configuration i)
 };
+
+// configuration (index within its query) that work item i of query Q solves
+__device__ inline long long config_of(const QDev& Q, long long i) { return Q.sel ? Q.sel[i] : i; }
 
 struct __align__(16) Ctl {
   long long item;       // global work item in the slot
@@ -667,7 +671,7 @@ __global__ void __launch_bounds__(kCols, kFP ? 2 : 4) sweep_kernel(Ctx x) {
     } else {  // U_DRAW: one word row of occupancy, 32 tubes per word
       const int tw = p.lo[U_DRAW] + rchunk;
       if (a < A) {
-        const long long rel = x.server ? c.item : c.item - Q.item0;
+        const long long rel = x.server ? c.item : config_of(Q, c.item - Q.item0);
         uint32_t word = 0;
         if (Q.occ_bits) {
           const uint32_t* cb = Q.occ_bits + (size_t)rel * Q.words_per_cfg;
@@ -804,7 +808,7 @@ __global__ void __launch_bounds__(kCols) control_kernel(Ctx x) {
     }
     if (tid == 0) {
       if (finish) {
-        const long long rel = x.server ? c.item : c.item - Q.item0;
+        const long long rel = x.server ? c.item : config_of(Q, c.item - Q.item0);
         Q.out.verdict[rel] = (uint8_t)verdict;
         if (Q.out.first_hit) Q.out.first_hit[rel] = fh;
         if (Q.out.mass) Q.out.mass[rel] = mass;
@@ -875,7 +879,7 @@ pc_status stream_plan_create(const StreamQuery* qs, int nq, cudaStream_t st, Str
   for (int i = 0; i < nq; ++i) {
     h[i].lat = stream_view(qs[i].lat); h[i].occ = qs[i].occ; h[i].occ_bits = qs[i].occ_bits;
     h[i].words_per_cfg = qs[i].words_per_cfg; h[i].n_cfg = qs[i].n_cfg; h[i].cfg0 = qs[i].cfg0;
-    h[i].out = qs[i].out; h[i].item0 = n_items; h[i].bits_only = qs[i].bits_only;
+    h[i].out = qs[i].out; h[i].item0 = n_items; h[i].bits_only = qs[i].bits_only; h[i].sel = qs[i].sel;
     n_items += qs[i].n_cfg;
     slot = std::max(slot, slot_bytes_of(qs[i].lat.A, qs[i].lat.L, qs[i].lat.P2));
     max_steps = std::max<unsigned long long>(max_steps, (unsigned long long)qs[i].lat.N + 4);
@@ -1144,7 +1148,7 @@ pc_status server_engine_set_query(ServerEngine* E, int qi, const StreamQuery& sq
   ch.base = qi; ch.n = 1;
   QDev& d = ch.q[0];
   d.lat = stream_view(sq.lat); d.occ = sq.occ; d.occ_bits = sq.occ_bits; d.words_per_cfg = sq.words_per_cfg;
-  d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0; d.bits_only = sq.bits_only;
+  d.n_cfg = sq.n_cfg; d.cfg0 = sq.cfg0; d.out = sq.out; d.item0 = 0; d.bits_only = sq.bits_only; d.sel = nullptr;
   upload_queries_kernel<<<1, kQChunk, 0, st>>>((QDev*)E->x.qs, ch);
   PC_CUDA(cudaGetLastError());
   PC_CUDA(cudaMemsetAsync(E->x.qnext + qi, 0, sizeof(unsigned long long), st));
@@ -1188,6 +1192,52 @@ pc_status server_engine_status(ServerEngine* E, cudaStream_t st, int buf, const 
 
 // Single-query convenience used by pc_inspect: build, run, release (stream
 // ordered; no host synchronisation).
+namespace {
+// configurations whose verdict is 1, in any order (each configuration's
+// solve does not depend on its slot)
+__global__ void select_percolating_kernel(const uint8_t* verdict, int64_t n, int64_t* sel,
+                                          unsigned long long* count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (verdict[i]) sel[atomicAdd(count, 1ull)] = i;
+}
+}  // namespace
+
+pc_status run_stream_verdict_first(const StreamJob& job, cudaStream_t st) {
+  if (job.n_cfg <= 0) return PC_OK;
+  // 1. the exact reached set decides every configuration (mass written 0)
+  StreamJob b = job;
+  b.bits_only = 1;
+  pc_status rc = run_stream(b, st);
+  if (rc) return rc;
+  // 2. the FP32 recursion on the percolating configurations only: the same
+  // steps as the single pass, so every output equals it to the bit
+  char* mem = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&mem, 256 + sizeof(int64_t) * (size_t)job.n_cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "verdict-first selection");
+  unsigned long long* cnt = (unsigned long long*)mem;
+  int64_t* sel = (int64_t*)(mem + 256);
+  unsigned long long n_sel = 0;
+  e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    const int grid = (int)std::min<int64_t>((job.n_cfg + 255) / 256, 1024);
+    select_percolating_kernel<<<grid, 256, 0, st>>>(job.out.verdict, job.n_cfg, sel, cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n_sel, cnt, sizeof(n_sel), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) rc = cuda_fail(e, "verdict-first selection");
+  if (rc == PC_OK && n_sel > 0) {
+    StreamJob f = job;
+    f.bits_only = 0;
+    f.sel = sel;
+    f.n_cfg = (int64_t)n_sel;
+    f.out.n_perc = nullptr;  // counted by the first pass
+    rc = run_stream(f, st);
+  }
+  cudaFreeAsync(mem, st);
+  return rc;
+}
+
 pc_status run_stream(const StreamJob& job, cudaStream_t st) {
   if (job.n_cfg <= 0) return PC_OK;
   if (job.bits_only) {  // verdict only: 32 steps per visit of a slab where a cluster holds the lattice
@@ -1197,7 +1247,7 @@ pc_status run_stream(const StreamJob& job, cudaStream_t st) {
   }
   StreamQuery q;
   q.lat = job.lat; q.occ = job.occ; q.occ_bits = job.occ_bits; q.words_per_cfg = job.words_per_cfg;
-  q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out; q.bits_only = job.bits_only;
+  q.n_cfg = job.n_cfg; q.cfg0 = job.cfg0; q.out = job.out; q.bits_only = job.bits_only; q.sel = job.sel;
   StreamPlan* P = nullptr;
   pc_status rc = stream_plan_create(&q, 1, st, &P);
   if (rc) return rc;

@@ -82,10 +82,32 @@ def test_wires_exact():
     assert np.array_equal(out["mass"], g["mass"])
 
 
-def test_streamed_solver_accepts_the_flag():
-    a = pc.pc_inspect(8, 90, 0.2, 7, 0, 60, mode=pc.PC_MODE_STREAM)
-    b = pc.pc_inspect(8, 90, 0.2, 7, 0, 60, mode=pc.PC_MODE_STREAM, verdict_first=True)
-    _identical(a, b, "streamed")
+@pytest.mark.parametrize("W,L,p,n", [
+    (8, 90, 0.2, 60),     # verdict pass on a one-CTA cluster
+    (20, 300, 0.2, 100),  # two CTAs
+    (32, 200, 0.17, 40),  # four CTAs
+    (64, 120, 0.16, 12),  # sixteen CTAs
+    (65, 40, 0.2, 6),     # wider than a cluster holds: step-synchronous verdict pass
+    (20, 64, 0.0, 8),     # nothing percolates: no FP32 pass at all
+])
+def test_streamed_verdict_first_equals_the_single_pass(W, L, p, n):
+    """Streamed path: a verdict-only solve of every configuration, then the
+    full solve of the percolating ones (outputs at their own indices)."""
+    a = pc.pc_inspect(W, L, p, 7, 3, n, mode=pc.PC_MODE_STREAM)
+    b = pc.pc_inspect(W, L, p, 7, 3, n, mode=pc.PC_MODE_STREAM, verdict_first=True)
+    _identical(a, b, (W, L, p))
+
+
+def test_streamed_verdict_first_device_outputs():
+    import torch
+    W, L, p, n = 20, 150, 0.19, 80
+    a = pc.pc_inspect(W, L, p, 9, 0, n, mode=pc.PC_MODE_STREAM)
+    b = pc.pc_inspect(W, L, p, 9, 0, n, mode=pc.PC_MODE_STREAM, verdict_first=True, device=True)
+    torch.cuda.synchronize()
+    b = {k: v.cpu().numpy() for k, v in b.items()}
+    for k in KEYS:
+        assert np.array_equal(np.asarray(a[k]), b[k]), k
+    assert int(b["n_percolating"][0]) == a["n_percolating"]
 
 
 def test_batch_with_the_flag():
