@@ -180,7 +180,8 @@ typedef struct pc_query {
 typedef struct pc_result {
   int64_t n_percolating;
   double Pi;
-  int32_t solver;           /* 0 = shared-memory resident, 1 = streamed */
+  int32_t solver;           /* 0 = shared-memory resident, 1 = streamed,
+                               2 = verdict-only with temporal blocking */
   int32_t threads;          /* CTA size the resident solver ran with */
 } pc_result;
 
@@ -204,7 +205,10 @@ typedef struct pc_result {
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
  * and PC_VERDICT_FIRST apply to every query of the batch; any other flag bit
- * is PC_ERR_ARG.
+ * is PC_ERR_ARG.  With PC_BITS_ONLY and without PC_ASYNC, a streamed query
+ * whose cross-section one thread-block cluster holds (pc_bits_blocked_shape)
+ * runs on the verdict-only solver with temporal blocking, on cuda_stream
+ * after the graph (solver 2 in out).
  * Results equal those of pc_inspect on each query.
  * Threads: calls from several host threads are safe.  A cached batch is
  * reference counted, so evicting it (or pc_shutdown) never frees one that a

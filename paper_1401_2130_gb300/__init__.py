@@ -360,7 +360,8 @@ def pc_batch_run(specs, *, device: bool = False, async_: bool = False, stream=No
     if res is None:
         return outs, None
     results = [{"n_percolating": r.n_percolating, "Pi": r.Pi,
-                "solver": "resident" if r.solver == 0 else "streamed", "threads": r.threads}
+                "solver": {0: "resident", 1: "streamed", 2: "blocked"}.get(r.solver, str(r.solver)),
+                "threads": r.threads}
                for r in res]
     if not device:
         for o, r in zip(outs, results):

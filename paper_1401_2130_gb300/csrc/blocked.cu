@@ -166,17 +166,43 @@ __device__ inline void take(const BCtx& x, BSlot& c, unsigned long long item) {
   plan_slot(x, c);
 }
 
+// Exclusive prefix over the slots of their pass items, by one block (each
+// thread a contiguous run of slots, then a scan of the per-thread sums).
 // Other CTAs wrote the slot records: they are read through L2 (__ldcg), not
 // from a line this SM's L1 may hold from before.
 __device__ void prefix_items(const BCtx& x) {
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int s = 0; s < x.K; ++s) {
-      x.pre[s] = acc;
-      acc += __ldcg(&x.slot[s].tiles) + __ldcg(&x.slot[s].draws);
-    }
-    x.pre[x.K] = acc;
+  __shared__ int s_part[32];
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int per = (x.K + T - 1) / T;
+  const int b0 = min(tid * per, x.K), b1 = min(b0 + per, x.K);
+  int sum = 0;
+  for (int s = b0; s < b1; ++s) sum += __ldcg(&x.slot[s].tiles) + __ldcg(&x.slot[s].draws);
+  const int lane = tid & 31, warp = tid >> 5;
+  int v = sum;  // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
   }
+  if (lane == 31) s_part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < (T >> 5) ? s_part[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += n;
+    }
+    s_part[lane] = w;
+  }
+  __syncthreads();
+  int run = v - sum + (warp ? s_part[warp - 1] : 0);
+  for (int s = b0; s < b1; ++s) {
+    x.pre[s] = run;
+    run += __ldcg(&x.slot[s].tiles) + __ldcg(&x.slot[s].draws);
+  }
+  if (tid == T - 1) x.pre[x.K] = run;
+  __syncthreads();
 }
 
 __global__ void blocked_init_kernel(BCtx x) {
@@ -185,6 +211,7 @@ __global__ void blocked_init_kernel(BCtx x) {
     take(x, c, (unsigned long long)s);
     x.slot[s] = c;
   }
+  __threadfence();  // the prefix reads the records through L2
   __syncthreads();
   prefix_items(x);
   if (threadIdx.x == 0) {
@@ -515,6 +542,11 @@ bool pick_shape(const Lattice& lat, Shape* out) {
   return false;
 }
 
+bool blocked_takes(const Lattice& lat) {
+  Shape sh;
+  return !std::getenv("PC_BITS_STEPWISE") && pick_shape(lat, &sh);
+}
+
 pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   *handled = false;
   if (!job.bits_only || job.sel || job.n_cfg <= 0 || std::getenv("PC_BITS_STEPWISE")) return PC_OK;
@@ -526,8 +558,9 @@ pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   cudaMemGetInfo(&free_b, &total_b);
   long long kmax = (long long)(free_b / 2 / (slot_words * 4 + 64));
   // enough slots that every cluster has slabs to take, as far as memory allows
-  long long K = std::min<long long>(job.n_cfg, std::max(8, 4 * sh.clusters));
-  K = std::min<long long>(K, std::min<long long>(kmax, 4096));
+  // as many configurations in flight as memory allows (short-lived ones
+  // leave little work per pass otherwise)
+  long long K = std::min<long long>(job.n_cfg, std::min<long long>(kmax, 4096));
   if (K < 1) { set_error("verdict-only solver: no memory for one configuration"); return PC_ERR_OOM; }
 
   const size_t head = 256 + a256_host(sizeof(BSlot) * (size_t)K) + a256_host(4 * (size_t)(K + 1));

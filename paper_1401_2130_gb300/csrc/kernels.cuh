@@ -96,6 +96,8 @@ pc_status run_stream_verdict_first(const StreamJob& job, cudaStream_t st);
 // job when a thread-block cluster holds the lattice's cross-section
 // (*handled = true), else leaves it to the step-synchronous solver.
 pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled);
+// Whether run_blocked takes PC_BITS_ONLY jobs of this lattice on this device.
+bool blocked_takes(const Lattice& lat);
 
 // Server engine (stream.cu): streamed-solver slots bound to queries by the host.
 struct ServerEngine;

@@ -120,3 +120,28 @@ def test_blocked_fixed_count_occupancy():
     occ = oracle.occupancy_fixed(W, L, Np, seed, 0, n)
     ref = oracle.inspect(W, L, occ=occ, mode="bfs", threads=THREADS)
     _check(g, ref, "fixed count")
+
+
+def test_blocked_in_verdict_only_batches():
+    """pc_batch_run with PC_BITS_ONLY: the streamed queries that a cluster
+    holds run on the blocked solver (solver "blocked"), the others as before;
+    results equal pc_inspect's and the oracle's.  PC_ASYNC batches keep the
+    step-synchronous slots."""
+    import torch
+    specs = [(4, 8, 0.2, 3, 0, 400), (20, 400, 0.19, 3, 5, 64), (32, 300, 0.17, 4, 0, 24),
+             (12, 200, 0.17, 3, 0, 64), (8, 64, 0.18, 3, 100, 300)]
+    outs, res = pc.pc_batch_run(specs, bits_only=True)
+    for sp, o, r in zip(specs, outs, res):
+        W, L, p, seed, b, n = sp
+        ref = oracle.inspect(W, L, p=p, seed=seed, cfg0=b, n=n, mode="bfs", threads=THREADS)
+        _check(o, ref, sp)
+        assert r["n_percolating"] == int(ref["verdict"].sum())
+        step = _stepwise(W, L, p, seed, b, n, bits_only=True)
+        _check(o, step, (sp, "step-synchronous"))
+        want = "resident" if (W, L) in ((4, 8), (8, 64)) else "blocked"
+        assert r["solver"] == want, (sp, r["solver"])
+    # asynchronous batch: device outputs, step-synchronous slots, same results
+    outs_a, _ = pc.pc_batch_run(specs, bits_only=True, device=True, async_=True)
+    torch.cuda.synchronize()
+    for sp, o, oa in zip(specs, outs, outs_a):
+        _check({k: v.cpu().numpy() for k, v in oa.items() if k in ("verdict", "first_hit", "m_stop")}, o, sp)
