@@ -292,7 +292,6 @@ BITS_BYTES_PER_SU = 0.375
 # occupancy word and its 12 contacts' words, and stores one word: 60 B / 32)
 BLOCKED_DRAM_BYTES_PER_SU = 24.80e6 / (4 * 12481 * 32 * (1890 + 1921) / 2)
 BLOCKED_SMEM_BYTES_PER_SU = 60 / 32
-BLOCKED_CHUNK = 16  # ticks the host launches between reads of the completion count
 
 
 def batching_specs(n=10_000):
@@ -302,13 +301,13 @@ def batching_specs(n=10_000):
 def blocked_launches(verdict, first_hit, m_stop) -> int:
     """Kernels of one verdict-only solve by the blocked solver whose
     configurations all hold a slot at once: the init kernel, then a pass and a
-    control kernel per tick, launched in chunks; one tick draws the first
-    rows, then one tick per 32 steps of the longest configuration."""
+    control kernel per tick inside the graph's WHILE node; one tick draws the
+    first rows, then one tick per 32 steps of the longest configuration."""
     v = np.asarray(verdict) != 0
     last = np.where(v, np.asarray(first_hit) - 1, np.asarray(m_stop))  # terminating step (0: none)
     passes = np.where(last >= 1, (last - 1) // 32 + 1, 0)
     ticks = 1 + int(passes.max(initial=0))
-    return 1 + 2 * BLOCKED_CHUNK * (-(-ticks // BLOCKED_CHUNK))
+    return 1 + 2 * ticks
 
 
 def solve_ticks(verdict, first_hit, m_stop) -> int:

@@ -140,7 +140,11 @@ pc_status pc_occupancy_fixed(int32_t W, int32_t L, int64_t n_metallic, uint64_t 
  * Errors: PC_ERR_ARG, PC_ERR_OOM, PC_ERR_CUDA, PC_ERR_INTERNAL, and
  * PC_ERR_TIMEOUT if a bounded device wait of the streamed solver expires
  * (host outputs only: with PC_OUT_DEVICE the call returns before the device
- * work ends).
+ * work ends, except with PC_VERDICT_FIRST on the streamed path).
+ * Solvers: the resident one where a configuration's state fits one CTA's
+ * shared memory, else the streamed one; with PC_BITS_ONLY the streamed path
+ * runs 32 steps per visit of a slab where one thread-block cluster holds the
+ * cross-section (pc_bits_blocked_shape).
  */
 pc_status pc_inspect(int32_t W, int32_t L, double p, uint64_t seed,
                      int64_t config_begin, int64_t n_configs,

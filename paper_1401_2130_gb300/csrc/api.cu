@@ -176,7 +176,7 @@ pc_status inspect_impl(int32_t W, int32_t L, double p, uint64_t seed, int64_t cf
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) { rc = cuda_fail(e, "copy outputs"); break; }
       if (err & 2) { set_error("streamed solver: a bulk-copy wait timed out"); rc = PC_ERR_TIMEOUT; break; }
-      if (err) { set_error("streamed solver: tick bound or segment check failed"); rc = PC_ERR_INTERNAL; break; }
+      if (err) { set_error("streamed solver: tick bound or device check failed"); rc = PC_ERR_INTERNAL; break; }
       if (n_percolating) *n_percolating = (int64_t)cnt;
       if (Pi) *Pi = (double)cnt / (double)n;
     }

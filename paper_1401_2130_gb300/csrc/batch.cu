@@ -319,6 +319,9 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
           P.solver = 2;
           StreamJob j;
           static_cast<StreamQuery&>(j) = s;
+          // error flag in the counter area the graph zeroes (past the three
+          // resident work counters)
+          j.error_out = (int*)((char*)(ctr + 2 * nq) + 32);
           b->blocked.push_back(j);
           continue;
         }
@@ -421,8 +424,9 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
     PC_CUDA(cudaEventRecord(b->done, st));
     return PC_OK;
   }
-  int err = 0;
+  int err = 0, err_b = 0;
   if (b->plan) PC_CUDA(cudaMemcpyAsync(&err, stream_plan_error(b->plan), sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (!b->blocked.empty()) PC_CUDA(cudaMemcpyAsync(&err_b, b->blocked[0].error_out, sizeof(int), cudaMemcpyDeviceToHost, st));
   std::vector<unsigned long long> cnt((size_t)nq);
   for (int64_t i = 0; i < nq; ++i) {
     const QueryPlan& P = b->qp[i];
@@ -439,6 +443,7 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
   PC_CUDA(cudaStreamSynchronize(st));
   if (err & 2) { set_error("streamed solver: a bulk-copy wait timed out"); return PC_ERR_TIMEOUT; }
   if (err) { set_error("streamed solver: tick bound or segment check failed"); return PC_ERR_INTERNAL; }
+  if (err_b) { set_error("verdict-only solver: pass bound reached"); return PC_ERR_INTERNAL; }
   for (int64_t i = 0; i < nq; ++i) {
     if (!dev_out && q[i].n_percolating) *q[i].n_percolating = (int64_t)cnt[i];
     if (out) {

@@ -41,8 +41,11 @@
 //
 // One tick = one pass kernel (persistent clusters taking slabs and draw
 // rows from a counter) and one control kernel (one CTA per slot: masks ->
-// outputs, refill, plan of the next pass).  The host launches ticks in
-// chunks and reads the completion count between chunks.
+// outputs, refill, plan of the next pass).  The ticks run inside one CUDA
+// graph's conditional WHILE node, whose condition the control kernel's last
+// CTA sets, so the call stays asynchronous; with PC_STREAM_HOST_LOOP set the
+// host launches them in chunks instead (profilers do not look inside graphs
+// with conditional nodes).
 #include <algorithm>
 #include <cstdlib>
 
@@ -91,10 +94,15 @@ struct BCtx {
   unsigned long long* n_done;
   unsigned* next_item;
   unsigned* arrive;
-  unsigned* ticks;             // passes run (diagnostics)
+  unsigned long long* ticks;   // passes run
   int cpr;                     // columns per CTA of a cluster
   int nrow;                    // slab rows in shared memory
   int nw;                      // valid rows per slab (nrow - 2)
+  int use_cond;                // set the WHILE condition at the end of a pass
+  int* error;                  // 1: the pass bound was reached (no correct run does)
+  unsigned long long max_ticks;
+  cudaGraphConditionalHandle cond;
+  int cs;                      // CTAs per cluster the kernel was planned for
 };
 
 // --- cluster primitives (PTX ISA: mapa, ld.shared::cluster, barrier.cluster)
@@ -216,7 +224,7 @@ __global__ void blocked_init_kernel(BCtx x) {
   prefix_items(x);
   if (threadIdx.x == 0) {
     *x.work = (unsigned long long)x.K;
-    *x.n_done = 0ull; *x.next_item = 0u; *x.arrive = 0u; *x.ticks = 0u;
+    *x.n_done = 0ull; *x.next_item = 0u; *x.arrive = 0u; *x.ticks = 0ull; *x.error = 0;
   }
 }
 
@@ -257,6 +265,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
   __shared__ int s_item[2];
   __shared__ unsigned s_g, s_h;
   const int tid = threadIdx.x, nt = blockDim.x;
+  {
+    // launched without the planned cluster shape: no distributed shared
+    // memory access; every CTA of the (same-sized) cluster returns here
+    uint32_t ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+    if ((int)ncta != x.cs) {
+      if (tid == 0) atomicOr(x.error, 4);
+      return;
+    }
+  }
   const uint32_t rank = cluster_rank();
   const int A = x.lat.A, L = x.lat.L, TW = x.lat.TW;
   const int stride = x.cpr + 1;                 // columns per quad row (column cpr: zero)
@@ -492,7 +510,13 @@ __global__ void __launch_bounds__(kCtlThreads) blocked_control_kernel(BCtx x) {
   if (tid == 0) {
     *x.arrive = 0u;
     *x.next_item = 0u;
-    *x.ticks += 1u;
+    const unsigned long long t = *x.ticks + 1ull;
+    *x.ticks = t;
+    if (x.use_cond) {  // the loop ends when every configuration is done
+      const bool more = __ldcg(x.n_done) < (unsigned long long)x.n_cfg;
+      if (more && t >= x.max_ticks) *x.error = 1;
+      cudaGraphSetConditional(x.cond, (more && t < x.max_ticks) ? 1u : 0u);
+    }
   }
 }
 
@@ -564,6 +588,7 @@ pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   if (K < 1) { set_error("verdict-only solver: no memory for one configuration"); return PC_ERR_OOM; }
 
   const size_t head = 256 + a256_host(sizeof(BSlot) * (size_t)K) + a256_host(4 * (size_t)(K + 1));
+  static_assert(sizeof(unsigned long long) * 3 + 4 * 3 <= 256, "counters fit the head");
   char* mem = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&mem, head + slot_words * 4 * (size_t)K, st);
   if (e != cudaSuccess) return cuda_fail(e, "verdict-only solver state");
@@ -571,52 +596,106 @@ pc_status run_blocked(const StreamJob& job, cudaStream_t st, bool* handled) {
   x.lat = lat; x.occ = job.occ; x.occ_bits = job.occ_bits; x.words_per_cfg = job.words_per_cfg;
   x.n_cfg = job.n_cfg; x.cfg0 = job.cfg0; x.out = job.out; x.K = (int)K;
   unsigned long long* ctr = (unsigned long long*)mem;
-  x.work = ctr; x.n_done = ctr + 1;
-  x.next_item = (unsigned*)(ctr + 2); x.arrive = x.next_item + 1; x.ticks = x.next_item + 2;
+  x.work = ctr; x.n_done = ctr + 1; x.ticks = ctr + 2;
+  x.next_item = (unsigned*)(ctr + 3); x.arrive = x.next_item + 1; x.error = (int*)(x.next_item + 2);
   x.slot = (BSlot*)(mem + 256);
   x.pre = (int*)(mem + 256 + a256_host(sizeof(BSlot) * (size_t)K));
   x.pool = (uint32_t*)(mem + head);
   x.slot_words = slot_words;
   x.cpr = sh.cpr; x.nrow = sh.nrow; x.nw = sh.nrow - 2;
-
-  pc_status rc = PC_OK;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)sh.cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3((unsigned)(sh.cs * sh.clusters)); cfg.blockDim = dim3((unsigned)sh.threads);
-  cfg.dynamicSmemBytes = (size_t)sh.smem; cfg.stream = st; cfg.attrs = at; cfg.numAttrs = 1;
-  // a configuration needs at most (sites / 32 + 2) passes: the reached set
+  // a configuration needs at most (sites / 32 + 3) passes: the reached set
   // grows by at least one site per step until it stops
   const long long per_cfg = (long long)(lat.N / kSteps) + 3;
   const long long rounds = (job.n_cfg + K - 1) / K;
-  const unsigned long long max_ticks = (unsigned long long)std::min<long long>(per_cfg * rounds, 1ll << 40);
-  unsigned long long* done_h = nullptr;
-  e = cudaMallocHost((void**)&done_h, sizeof(unsigned long long));
-  if (e != cudaSuccess) { cudaFreeAsync(mem, st); return cuda_fail(e, "pinned count"); }
-  *done_h = 0;
-  blocked_init_kernel<<<1, 256, 0, st>>>(x);
-  e = cudaGetLastError();
-  unsigned long long ticks = 0;
-  while (e == cudaSuccess && *done_h < (unsigned long long)job.n_cfg) {
-    for (int i = 0; i < kChunk && e == cudaSuccess; ++i) {
-      e = cudaLaunchKernelEx(&cfg, blocked_pass_kernel, x);
-      if (e == cudaSuccess) {
-        blocked_control_kernel<<<x.K, kCtlThreads, 0, st>>>(x);
-        e = cudaGetLastError();
+  x.max_ticks = (unsigned long long)std::min<long long>(per_cfg * rounds, 1ll << 40);
+  x.use_cond = 0;
+  x.cond = 0;
+  x.cs = sh.cs;
+
+  pc_status rc = PC_OK;
+  const unsigned grid = (unsigned)(sh.cs * sh.clusters);
+  if (std::getenv("PC_STREAM_HOST_LOOP")) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)sh.cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(grid); cfg.blockDim = dim3((unsigned)sh.threads);
+    cfg.dynamicSmemBytes = (size_t)sh.smem; cfg.stream = st; cfg.attrs = at; cfg.numAttrs = 1;
+    unsigned long long* done_h = nullptr;
+    e = cudaMallocHost((void**)&done_h, sizeof(unsigned long long));
+    if (e != cudaSuccess) { cudaFreeAsync(mem, st); return cuda_fail(e, "pinned count"); }
+    *done_h = 0;
+    blocked_init_kernel<<<1, 256, 0, st>>>(x);
+    e = cudaGetLastError();
+    unsigned long long ticks = 0;
+    while (e == cudaSuccess && *done_h < (unsigned long long)job.n_cfg) {
+      for (int i = 0; i < kChunk && e == cudaSuccess; ++i) {
+        e = cudaLaunchKernelEx(&cfg, blocked_pass_kernel, x);
+        if (e == cudaSuccess) {
+          blocked_control_kernel<<<x.K, kCtlThreads, 0, st>>>(x);
+          e = cudaGetLastError();
+        }
+      }
+      ticks += kChunk;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(done_h, x.n_done, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess && ticks > x.max_ticks && *done_h < (unsigned long long)job.n_cfg) {
+        set_error("verdict-only solver did not converge");
+        rc = PC_ERR_INTERNAL;
+        break;
       }
     }
-    ticks += kChunk;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(done_h, x.n_done, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && ticks > max_ticks && *done_h < (unsigned long long)job.n_cfg) {
-      set_error("verdict-only solver did not converge");
-      rc = PC_ERR_INTERNAL;
-      break;
+    int err = 0;
+    if (e == cudaSuccess && rc == PC_OK) {
+      e = cudaMemcpyAsync(&err, x.error, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
+    if (e != cudaSuccess) rc = cuda_fail(e, "verdict-only solver");
+    else if (err) { set_error("verdict-only solver: device check failed"); rc = PC_ERR_INTERNAL; }
+    cudaFreeHost(done_h);
+    cudaFreeAsync(mem, st);
+    *handled = true;
+    return rc;
   }
-  if (e != cudaSuccess) rc = cuda_fail(e, "verdict-only solver");
-  cudaFreeHost(done_h);
+  // init -> WHILE(pass, control), one graph
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  do {
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) break;
+    if ((e = cudaGraphConditionalHandleCreate(&x.cond, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    x.use_cond = 1;
+    void* args[] = {&x};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void*)blocked_init_kernel;
+    kp.gridDim = dim3(1); kp.blockDim = dim3(256); kp.kernelParams = args;
+    cudaGraphNode_t n_init, n_while, n_pass, n_ctl;
+    if ((e = cudaGraphAddKernelNode(&n_init, g, nullptr, 0, &kp)) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = x.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_while, g, &n_init, nullptr, 1, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaKernelNodeParams pp = {};
+    pp.func = (void*)blocked_pass_kernel;
+    pp.gridDim = dim3(grid); pp.blockDim = dim3((unsigned)sh.threads);
+    pp.sharedMemBytes = (unsigned)sh.smem; pp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&n_pass, body, nullptr, 0, &pp)) != cudaSuccess) break;
+    cudaKernelNodeAttrValue cv = {};
+    cv.clusterDim.x = (unsigned)sh.cs; cv.clusterDim.y = 1; cv.clusterDim.z = 1;
+    if ((e = cudaGraphKernelNodeSetAttribute(n_pass, cudaLaunchAttributeClusterDimension, &cv)) != cudaSuccess) break;
+    cudaKernelNodeParams cpk = {};
+    cpk.func = (void*)blocked_control_kernel;
+    cpk.gridDim = dim3((unsigned)x.K); cpk.blockDim = dim3(kCtlThreads); cpk.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&n_ctl, body, &n_pass, 1, &cpk)) != cudaSuccess) break;
+    if ((e = cudaGraphInstantiate(&ex, g, 0)) != cudaSuccess) break;
+    if ((e = cudaGraphLaunch(ex, st)) != cudaSuccess) break;
+    if (job.error_out) e = cudaMemcpyAsync(job.error_out, x.error, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  } while (0);
+  if (e != cudaSuccess) rc = cuda_fail(e, "verdict-only solver graph");
+  if (ex) cudaGraphExecDestroy(ex);  // an in-flight executable is freed on completion
+  if (g) cudaGraphDestroy(g);
   cudaFreeAsync(mem, st);
   *handled = true;
   return rc;

@@ -1223,9 +1223,13 @@ pc_status run_stream_verdict_first(const StreamJob& job, cudaStream_t st) {
     select_percolating_kernel<<<grid, 256, 0, st>>>(job.out.verdict, job.n_cfg, sel, cnt);
     e = cudaGetLastError();
   }
+  int err1 = 0;  // the verdict pass's error flag: the FP32 pass rewrites error_out
   if (e == cudaSuccess) e = cudaMemcpyAsync(&n_sel, cnt, sizeof(n_sel), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && job.error_out)
+    e = cudaMemcpyAsync(&err1, job.error_out, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) rc = cuda_fail(e, "verdict-first selection");
+  else if (err1) { set_error("verdict pass: a device bound was reached"); rc = (err1 & 2) ? PC_ERR_TIMEOUT : PC_ERR_INTERNAL; }
   if (rc == PC_OK && n_sel > 0) {
     StreamJob f = job;
     f.bits_only = 0;

@@ -145,3 +145,25 @@ def test_blocked_in_verdict_only_batches():
     torch.cuda.synchronize()
     for sp, o, oa in zip(specs, outs, outs_a):
         _check({k: v.cpu().numpy() for k, v in oa.items() if k in ("verdict", "first_hit", "m_stop")}, o, sp)
+
+
+def test_blocked_device_outputs():
+    """PC_OUT_DEVICE: the passes run inside one graph, asynchronously; the
+    device outputs equal the host ones."""
+    import torch
+    W, L, p, seed, n = 20, 300, 0.19, 11, 96
+    h = pc.pc_inspect(W, L, p, seed, 0, n, mode=pc.PC_MODE_STREAM, bits_only=True)
+    d = pc.pc_inspect(W, L, p, seed, 0, n, mode=pc.PC_MODE_STREAM, bits_only=True, device=True)
+    torch.cuda.synchronize()
+    d = {k: v.cpu().numpy() for k, v in d.items()}
+    _check(d, h, "device outputs")
+    assert int(d["n_percolating"][0]) == h["n_percolating"]
+
+
+def test_blocked_host_loop_equals_graph(monkeypatch):
+    """The host-driven passes (for profilers) give the graph's results."""
+    W, L, p, seed, n = 32, 400, 0.17, 12, 24
+    g = pc.pc_inspect(W, L, p, seed, 0, n, mode=pc.PC_MODE_STREAM, bits_only=True)
+    monkeypatch.setenv("PC_STREAM_HOST_LOOP", "1")
+    h = pc.pc_inspect(W, L, p, seed, 0, n, mode=pc.PC_MODE_STREAM, bits_only=True)
+    _check(h, g, "host loop")
