@@ -140,7 +140,7 @@ struct BatchGraph {
   size_t mem_bytes = 0;
   char* tab = nullptr;       // query tables of the persistent resident launches
   StreamPlan* plan = nullptr;
-  std::vector<StreamJob> blocked;  // verdict-only streamed queries run after the graph (blocked.cu)
+  std::vector<StreamJob> blocked;  // verdict-only streamed queries run after the batch graph (blocked.cu)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<QueryPlan> qp;
@@ -313,9 +313,9 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         s.out.n_perc = P.n_perc;
         s.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
         if (!s.out.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
-        if (s.bits_only && !(flags & PC_ASYNC) && blocked_takes(lat)) {
+        if (s.bits_only && blocked_takes(lat)) {
           // verdicts only, and a cluster holds the cross-section: 32 steps
-          // per visit of a slab, after the graph (a host-driven loop)
+          // per visit of a slab, after the batch graph (in a graph of its own)
           P.solver = 2;
           StreamJob j;
           static_cast<StreamQuery&>(j) = s;
@@ -409,7 +409,7 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
   PC_CUDA(cudaStreamWaitEvent(st, b->done, 0));
   PC_CUDA(cudaGraphLaunch(b->exec, st));
   // verdict-only streamed queries on the blocked solver, after the graph
-  // (which zeroes their counters); never in PC_ASYNC batches
+  // (which zeroes their counters), each in a graph of its own
   for (const StreamJob& j : b->blocked) {
     bool handled = false;
     pc_status rc = run_blocked(j, st, &handled);
