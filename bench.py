@@ -640,9 +640,11 @@ def run_serving(args, pc, torch):
         plain.append(pc.pc_inspect(*sp))
         svc.append(time.perf_counter() - t0)
     t_plain = float(sum(svc))
-    # a query may take up to 4,096 slots but at most half the arena (the
-    # server's bound): a large query gets about the slots its plain solve
-    # uses, and queries behind it are still admitted
+    # at most 1,024 slots a query in a 128 GB arena: a cap of 4,096 (200 GB)
+    # helps a short prefix (40 queries: 4,264 against 3,086 configurations/s
+    # at saturation) but lets one large query hold the arena and stop
+    # admission behind it on a longer one (100 queries: 512 against 590,
+    # open-loop p99 193 against 93 s)
     opts = dict(hbm_budget_bytes=args.serve_budget_gb << 30, max_slots=4096,
                 max_slots_per_query=args.serve_slots_per_query, ticks_per_poll=8, max_W=64)
 
@@ -906,8 +908,8 @@ def main():
     ap.add_argument("--configs-per-p", type=int, default=N_CFG,
                     help="smaller cases for profiling only; the benchmark workload is 10^4")
     ap.add_argument("--serve-queries", type=int, default=100)
-    ap.add_argument("--serve-budget-gb", type=int, default=200)
-    ap.add_argument("--serve-slots-per-query", type=int, default=4096)
+    ap.add_argument("--serve-budget-gb", type=int, default=128)
+    ap.add_argument("--serve-slots-per-query", type=int, default=1024)
     ap.add_argument("--large-configs", type=int, default=64)
     ap.add_argument("--large-block", type=int, default=8,
                     help="configurations per p in one step of the large workload")

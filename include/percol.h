@@ -209,10 +209,10 @@ typedef struct pc_result {
  * call synchronises cuda_stream and fills out; with PC_ASYNC (requires
  * PC_OUT_DEVICE and out == NULL) it returns after enqueueing.  PC_BITS_ONLY
  * and PC_VERDICT_FIRST apply to every query of the batch; any other flag bit
- * is PC_ERR_ARG.  With PC_BITS_ONLY, a streamed query whose cross-section
- * one thread-block cluster holds (pc_bits_blocked_shape) runs on the
- * verdict-only solver with temporal blocking, on cuda_stream after the
- * batch's graph (solver 2 in out).
+ * is PC_ERR_ARG.  With PC_BITS_ONLY and without PC_ASYNC, a streamed query
+ * whose cross-section one thread-block cluster holds (pc_bits_blocked_shape)
+ * runs on the verdict-only solver with temporal blocking, on cuda_stream
+ * after the batch's graph (solver 2 in out).
  * Results equal those of pc_inspect on each query.
  * Threads: calls from several host threads are safe.  A cached batch is
  * reference counted, so evicting it (or pc_shutdown) never frees one that a
@@ -231,11 +231,9 @@ pc_status pc_batch_run(const pc_query* queries, int64_t n_queries, pc_result* ou
  * Serving: a continuous-batching request loop on one device (the current
  * device at pc_server_create).  Queries are admitted in arrival order as soon
  * as their HBM footprint -- output buffers, plus the streamed solver's state
- * for max(1, min(slots free, max_slots_per_query, the slots that half the
- * arena holds)) configurations when the lattice exceeds shared memory --
- * fits the server's device arena of hbm_budget_bytes.  The half-arena bound
- * keeps one large query from holding the whole arena, so queries behind it
- * are admitted beside it.  Admitted queries run concurrently on the device:
+ * for max(1, min(slots free, max_slots_per_query)) configurations when the
+ * lattice exceeds shared memory -- fits the server's device arena of
+ * hbm_budget_bytes.  Admitted queries run concurrently on the device:
  * resident-size queries as persistent kernels on side streams, the others in
  * the streamed solver's slots, which refill on the device while the query
  * has configurations left.  New arrivals are admitted between chunks of

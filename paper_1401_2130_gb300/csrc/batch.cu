@@ -313,7 +313,7 @@ pc_status build_batch(const pc_query* q, int64_t nq, int32_t flags, cudaStream_t
         s.out.n_perc = P.n_perc;
         s.bits_only = (flags & PC_BITS_ONLY) ? 1 : 0;
         if (!s.out.verdict) { set_error("verdicts buffer required"); rc = PC_ERR_ARG; break; }
-        if (s.bits_only && blocked_takes(lat)) {
+        if (s.bits_only && !(flags & PC_ASYNC) && blocked_takes(lat)) {
           // verdicts only, and a cluster holds the cross-section: 32 steps
           // per visit of a slab, after the batch graph (in a graph of its own)
           P.solver = 2;
@@ -409,7 +409,8 @@ extern "C" pc_status pc_batch_run(const pc_query* q, int64_t nq, pc_result* out,
   PC_CUDA(cudaStreamWaitEvent(st, b->done, 0));
   PC_CUDA(cudaGraphLaunch(b->exec, st));
   // verdict-only streamed queries on the blocked solver, after the graph
-  // (which zeroes their counters), each in a graph of its own
+  // (which zeroes their counters), each in a graph of its own; not in
+  // PC_ASYNC batches
   for (const StreamJob& j : b->blocked) {
     bool handled = false;
     pc_status rc = run_blocked(j, st, &handled);

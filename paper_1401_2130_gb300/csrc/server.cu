@@ -221,9 +221,6 @@ void worker_main(pc_server* s) {
           long long k = std::min<long long>(q.n_configs, free_slots);
           k = std::min<long long>(k, std::max(1, s->opts.max_slots_per_query));
           k = std::min<long long>(k, (long long)(room / (sb + 256)));
-          // a bounded share: one query's slots take at most half the arena,
-          // so queries behind a large one can still be admitted beside it
-          k = std::min<long long>(k, std::max<long long>(1, (long long)(s->opts.hbm_budget_bytes / 2 / (sb + 256))));
           size_t soff = 0;
           if (k < 1 || !s->arena.alloc((size_t)k * sb, &soff)) { s->arena.release(off, ob); break; }
           t.kind = 1; t.qi = qi; t.off_out = off; t.bytes_out = ob;

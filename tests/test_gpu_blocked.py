@@ -125,8 +125,8 @@ def test_blocked_fixed_count_occupancy():
 def test_blocked_in_verdict_only_batches():
     """pc_batch_run with PC_BITS_ONLY: the streamed queries that a cluster
     holds run on the blocked solver (solver "blocked"), the others as before;
-    results equal the oracle's and the step-synchronous solver's, also in an
-    asynchronous batch with device outputs."""
+    results equal the oracle's and the step-synchronous solver's.  PC_ASYNC
+    batches keep the step-synchronous slots, with the same results."""
     import torch
     specs = [(4, 8, 0.2, 3, 0, 400), (20, 400, 0.19, 3, 5, 64), (32, 300, 0.17, 4, 0, 24),
              (12, 200, 0.17, 3, 0, 64), (8, 64, 0.18, 3, 100, 300)]
@@ -140,7 +140,7 @@ def test_blocked_in_verdict_only_batches():
         _check(o, step, (sp, "step-synchronous"))
         want = "resident" if (W, L) in ((4, 8), (8, 64)) else "blocked"
         assert r["solver"] == want, (sp, r["solver"])
-    # asynchronous batch with device outputs: same results
+    # asynchronous batch: device outputs, step-synchronous slots, same results
     outs_a, _ = pc.pc_batch_run(specs, bits_only=True, device=True, async_=True)
     torch.cuda.synchronize()
     for sp, o, oa in zip(specs, outs, outs_a):
