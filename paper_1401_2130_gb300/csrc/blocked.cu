@@ -49,6 +49,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "blocked_plan.h"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -56,13 +57,11 @@ namespace pc {
 
 namespace {
 
-constexpr int kSteps = 32;       // steps per pass (one word row of halo on each side)
+constexpr int kSteps = kPassSteps;
 constexpr int kMaxThreads = 800;  // columns per CTA: 80 registers a thread
 constexpr int kMaxQuads = 9;      // slab rows / 4 in shared memory (valid rows + 2 halo rows)
 constexpr int kCtlThreads = 256;
 constexpr int kChunk = 16;       // ticks launched between reads of the completion count
-
-enum : int { BP_EMPTY = 0, BP_DRAW0 = 1, BP_STEP = 2 };
 
 inline size_t a256_host(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -156,16 +155,8 @@ __device__ inline uint32_t draw_word(const BCtx& x, long long rel, int tw, int a
 
 // Items of a slot's next pass (slabs, then rows to draw).
 __device__ inline void plan_slot(const BCtx& x, BSlot& c) {
-  const int TW = x.lat.TW;
-  c.tiles = 0; c.draws = 0;
-  if (c.phase == BP_DRAW0) {
-    c.draws = TW < 2 ? TW : 2;  // rows 0 and 1: what the first pass reads
-  } else if (c.phase == BP_STEP) {
-    const int rtop = min((c.m0 + kSteps) >> 5, TW - 1);  // highest row 32 more steps can reach
-    c.tiles = (rtop + 1 + x.nw - 1) / x.nw;
-    // the next pass reads one row more: draw it now
-    if (c.G < TW && c.G <= ((c.m0 + 2 * kSteps) >> 5)) c.draws = 1;
-  }
+  const PassItems p = pass_items(c.phase, c.m0, c.G, x.lat.TW, x.nw);
+  c.tiles = p.tiles; c.draws = p.draws;
 }
 
 __device__ inline void take(const BCtx& x, BSlot& c, unsigned long long item) {
@@ -336,12 +327,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) blocked_pass_kernel(BCtx x) {
     }
 
     // slab: local row i holds word row w0 - 1 + i
-    const int w0 = local * x.nw;
-    const int m0 = c.m0;
-    const int rtop = min((m0 + kSteps) >> 5, TW - 1);
-    const int n_eff = min(x.nrow, rtop - w0 + 2);  // rows above rtop stay empty for 32 steps
-    const int q_eff = (n_eff + 3) >> 2;            // quads computed (rows past n_eff loaded as zero)
-    const int ivmax = min(x.nw, n_eff - 1);        // valid rows 1 .. ivmax
+    const Slab sb = slab_of(local, c.m0, TW, x.nw, x.nrow);
+    const int w0 = sb.w0, m0 = c.m0;
+    const int n_eff = sb.n_eff;              // rows above the top row stay empty for 32 steps
+    const int q_eff = (n_eff + 3) >> 2;      // quads computed (rows past n_eff loaded as zero)
+    const int ivmax = sb.ivmax;              // valid rows 1 .. ivmax
     const int iend = endw - (w0 - 1);
     const bool end_here = iend >= 1 && iend <= ivmax;
     if (own) {
@@ -469,16 +459,11 @@ __global__ void __launch_bounds__(kCtlThreads) blocked_control_kernel(BCtx x) {
       }
     } else {  // BP_STEP
       c.G += c.draws;
-      const unsigned g = c.gmask, h = c.hmask;
-      c.gmask = 0u; c.hmask = 0u;
       // first step of the pass that reached the detector or did not grow
-      const unsigned stop = h | ~g;
-      if (stop) {
-        const int j = __ffs((int)stop) - 1;
-        const int step = c.m0 + 1 + j;
-        finish = true;
-        if ((h >> j) & 1u) { verdict = 1; fh = step + 1; mstop = step + 1; }
-        else mstop = step;
+      const PassOutcome o = pass_outcome(c.gmask, c.hmask, c.m0);
+      c.gmask = 0u; c.hmask = 0u;
+      if (o.finish) {
+        finish = true; verdict = o.verdict; fh = o.first_hit; mstop = o.m_stop;
       } else {
         c.m0 += kSteps; c.par ^= 1;
       }

@@ -1,7 +1,10 @@
 """Host-side parts of the library, compiled with the host C++ compiler (no
 GPU): the server's HBM admission allocator (csrc/arena.h) against a granule
-model, the autotuner's file format (csrc/tune_file.h), and the streamed
-solver's tick planner (csrc/plan.h) simulated over many fibre lengths."""
+model, the autotuner's file format (csrc/tune_file.h), the streamed
+solver's tick planner (csrc/plan.h) simulated over many fibre lengths, and
+the verdict-only blocked solver's pass planner and mask decoding
+(csrc/blocked_plan.h) simulated over fibre lengths, slab heights and
+configuration histories."""
 from __future__ import annotations
 
 import os
@@ -43,5 +46,11 @@ def test_tune_file_round_trip_and_damaged_entries(tmp_path_factory, tmp_path):
 
 def test_tick_planner_keeps_every_read_ready(tmp_path_factory):
     exe = _compile(tmp_path_factory, "plan_check")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout[-3000:] + r.stderr
+
+
+def test_blocked_pass_planner_and_outcomes(tmp_path_factory):
+    exe = _compile(tmp_path_factory, "blocked_plan_check")
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout[-3000:] + r.stderr
