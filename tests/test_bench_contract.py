@@ -93,3 +93,25 @@ def test_sample_parity_block_flags_any_difference():
     f.plant = bench.PS[7]
     bad = bench.sample_parity(f, refs, 4)
     assert not bad["ok"] and bad["mismatched_configs"] == 1
+
+
+def test_launch_accounting_follows_the_solvers_tick_rules():
+    """gpu_launches of the large lines is counted from the outputs: the
+    streamed solver runs a draw tick, a preparation tick and one tick per
+    step of the longest configuration; the blocked verdict-only solver a draw
+    tick and one pass per 32 steps (its pass planner is simulated on the CPU
+    in test_host_parts), each tick one pass and one control kernel after one
+    init kernel."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    # three configurations: percolating at first_hit 100 (last step 99),
+    # stopping at m_stop 33, and none metallic at t = 0 (m_stop 0)
+    v = np.array([1, 0, 0]); fh = np.array([100, -1, -1]); ms = np.array([100, 33, 0])
+    assert bench.solve_ticks(v, fh, ms) == 99 + 3
+    # passes: step 99 lies in pass (99 - 1) // 32 + 1 = 4, step 33 in pass 2
+    assert bench.blocked_launches(v, fh, ms) == 1 + 2 * (1 + 4)
+    # a step exactly at a pass boundary: step 32 is the last of pass 1, 33 the first of pass 2
+    assert bench.blocked_launches(np.array([0]), np.array([-1]), np.array([32])) == 1 + 2 * 2
+    assert bench.blocked_launches(np.array([0]), np.array([-1]), np.array([33])) == 1 + 2 * 3
+    assert bench.blocked_launches(np.array([0]), np.array([-1]), np.array([0])) == 1 + 2 * 1
