@@ -134,3 +134,17 @@ def test_missing_library_fails_loudly(tmp_path):
             mod.load(str(tmp_path / "nope.so"))
     finally:
         mod._lib = saved
+
+
+def test_binding_constants_equal_the_header():
+    """Every PC_* flag and status the header defines has the same value in
+    the Python binding (the binding only marshals: a drifted constant would
+    send the wrong flag through the ABI)."""
+    import re
+    text = open(os.path.join(ROOT, "include", "percol.h")).read()
+    defs = dict(re.findall(r"#define (PC_[A-Z0-9_]+) \(?(-?(?:0x[0-9a-fA-F]+|\d+))\)?", text))
+    assert {"PC_OK", "PC_ERR_ARG", "PC_OUT_DEVICE", "PC_MODE_STREAM", "PC_BITS_ONLY", "PC_VERDICT_FIRST",
+            "PC_ASYNC"} <= set(defs)
+    for name, value in defs.items():
+        if hasattr(pc, name):
+            assert getattr(pc, name) == int(value, 0), name
